@@ -1,0 +1,380 @@
+"""Benchmark: zone-updates/s of full ADER-WENO steps on one GB300 (or N
+independent replicas under torchrun), with the ALU roofline of the dominant
+kernel, clocks during the timed region, an end-to-end number through the C
+ABI with host buffers, and the FP64 oracle timed on the host cores.
+
+Workload (headline): 3D Euler, Taylor-Green vortex on a periodic 256^3 grid,
+fourth-order WENO+ADER, HLLC, FP64, CFL 0.3 (device-resident dt).  One "step"
+is one full step of the method over the whole grid.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# ALU peaks from unit counts and the maximum SM clock: 152 SMs x 2 FP64 FMA
+# lanes/clk (x 128 FP32) x 2 flops x 2.07 GHz
+SMS, CLK = 152, 2.07e9
+PEAK_FP64 = SMS * 2 * 2 * CLK / 1e12      # 1.259 TFLOP/s
+PEAK_FP32 = SMS * 128 * 2 * CLK / 1e12    # 80.5 TFLOP/s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32-bulk form line")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "native":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region"""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.p is None:
+            return out
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out["sm_mhz"] = float(np.median(sm)) if sm else None
+        out["sm_max_mhz"] = max(mx) if mx else None
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+# --------------------------------------------------------------------------
+def workload(n):
+    from paper_2211_13295_gb300 import problems as P
+    return P.tgv3d(n=n, order=4, cfl=0.3)
+
+
+def workload_name(prob):
+    return f"tgv3d {prob.n[0]}^3 order {prob.order} HLLC CFL {prob.cfl} periodic"
+
+
+def gpu_state(prob):
+    """initial state generated on the host (exact zone averages), as a pinned tensor"""
+    import torch
+    U = prob.initial_state()
+    return torch.from_numpy(U).pin_memory()
+
+
+def time_steps(grid, steps, warmup, world):
+    import torch
+    grid.cfl_dt()
+    for _ in range(warmup):
+        grid.step(0.0, sync=False)
+    grid.check()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    grid.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        grid.step(0.0, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = grid.profile_read()
+    grid.profile(False)
+    grid.check()
+    return ms, prof
+
+
+def time_e2e(grid, Uh, steps, world):
+    """through the public API with host buffers: H2D of the state from pinned
+    memory, one step, D2H of the updated state, every step"""
+    import torch
+    out = torch.empty_like(Uh).pin_memory()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        grid.set_state(Uh.numpy())
+        grid.step(0.0, sync=False)
+        grid.get_state(out.numpy())
+    torch.cuda.synchronize()
+    barrier(world)
+    return (time.perf_counter() - t0) * 1e3
+
+
+def cpu_baseline_and_parity(prob, grid_state_after, U0, dt0, n_windows=3, m=4, seed=0):
+    """The FP64 oracle (a) timed on a bounded sample of the workload (a full
+    periodic 32^3 Taylor-Green grid, one step, all host cores) and (b) run on
+    windows of the full-size grid to state the L1 error of the GPU step."""
+    import oracle
+    from paper_2211_13295_gb300 import problems as P
+    cores = os.cpu_count()
+    small = P.tgv3d(n=32, order=prob.order, cfl=prob.cfl)
+    Us = small.initial_state()
+    orc = oracle.Oracle(small)
+    dts = orc.cfl_dt(Us, small.cfl)
+    t0 = time.perf_counter()
+    orc.step(Us, 0.0, dts)
+    el = time.perf_counter() - t0
+    base = {"value": small.zones / el, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"one step of tgv3d 32^3 order {prob.order} FP64 (32768 zones), {el:.1f} s wall"}
+    # parity on windows of the full-size first step
+    parity = None
+    if grid_state_after is not None:
+        g = prob.order
+        rng = np.random.default_rng(seed)
+        n = prob.n[0]
+        L = prob.hi[0] - prob.lo[0]
+        errs = []
+        for _ in range(n_windows):
+            c = rng.integers(0, n, size=3)
+            idx = [np.arange(c[d] - g, c[d] + m + g) % n for d in range(3)]
+            Ug = U0[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+            wprob = P.Problem("uniform", 3, (m, m, m), (0, 0, 0), (m * L / n,) * 3, prob.order,
+                              cfl=prob.cfl)
+            wo = oracle.Oracle(wprob)
+            Uo, _, rc = wo.step_ghosted(Ug, dt0)
+            sl = [np.arange(c[d], c[d] + m) % n for d in range(3)]
+            Ugpu = grid_state_after[:, sl[2]][:, :, sl[1]][:, :, :, sl[0]]
+            e = max(np.abs(Ugpu[v] - Uo[v]).sum() / np.abs(Uo[v]).sum() for v in range(5) if np.abs(Uo[v]).sum() > 0)
+            errs.append(e)
+        parity = max(errs)
+    return base, parity
+
+
+def run_native(args, rank, world, local):
+    import torch
+    from paper_2211_13295_gb300 import awe, build, opcount
+    build.build()
+    torch.cuda.set_device(local)
+    prob = workload(args.n)
+    Uh = gpu_state(prob)
+    grid = awe.Grid(prob, prec="fp64")
+    grid.set_state(Uh.numpy())
+    # one explicit step from the initial state for the stated error
+    dt0 = grid.cfl_dt()
+    grid.step(dt0)
+    U1 = grid.get_state() if rank == 0 and not args.no_cpu else None
+    grid.set_state(Uh.numpy())
+    grid.set_time(0.0)
+
+    clk = Clocks(local)
+    ms, prof = time_steps(grid, args.steps, args.warmup, world)
+    clocks = clk.stop()
+    ms = max_over_ranks(ms, world)
+    zones = prob.zones
+    value = world * zones * args.steps / (ms * 1e-3)
+
+    # dominant kernel: the predictor (FP64 pipe)
+    n_pred, ms_pred = prof["predictor"]
+    avg_pred = ms_pred / max(n_pred, 1)
+    flops_pred = opcount.predictor_flops_per_launch(prob)
+    achieved = flops_pred / (avg_pred * 1e-3) / 1e12
+    traffic = None
+    tr_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_file):
+        traffic = json.load(open(tr_file)).get("predictor_fp64_per_launch")
+    launches_per_step = sum(v[0] for v in prof.values()) / max(args.steps, 1)
+    # kernel launches of the timed region: profiled spans + 1 finalize per step
+    gpu_launches = int(round(sum(v[0] for k, v in prof.items()) + args.steps))
+
+    grid.set_state(Uh.numpy())
+    grid.cfl_dt()
+    e2e_ms = max_over_ranks(time_e2e(grid, Uh, max(1, min(args.steps, 3)), world), world)
+    e2e_steps = max(1, min(args.steps, 3))
+    nbytes = Uh.numel() * 8
+    grid.close()
+
+    forms = {}
+    if not args.no_forms:
+        g32 = awe.Grid(prob, prec="fp32")
+        g32.set_state(Uh.numpy())
+        dtf = g32.cfl_dt()
+        g32.step(dtf)
+        U1f = g32.get_state() if U1 is not None else None
+        g32.set_state(Uh.numpy())
+        ms32, prof32 = time_steps(g32, args.steps, args.warmup, world)
+        ms32 = max_over_ranks(ms32, world)
+        np32, mp32 = prof32["predictor"]
+        g32.close()
+        f32 = {"value": world * zones * args.steps / (ms32 * 1e-3), "ms_per_step": ms32 / args.steps,
+               "dtype": "f32 bulk, f64 update/weights/CFL",
+               "predictor_ms": mp32 / max(np32, 1),
+               "predictor_tflops": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12,
+               "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32}
+        if U1f is not None:
+            f32["rel_l1_vs_fp64_gpu_one_step"] = max(
+                float(np.abs(U1f[v] - U1[v]).sum() / np.abs(U1[v]).sum()) for v in range(5) if np.abs(U1[v]).sum() > 0)
+        forms["fp32_bulk"] = f32
+
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, parity = cpu_baseline_and_parity(prob, U1, Uh.numpy(), dt0)
+
+    if rank == 0:
+        line = {
+            "metric": "zone-updates/sec per full ADER-WENO step at stated L1 error vs FP64 oracle",
+            "value": value,
+            "unit": "zone-updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(prob), "n": prob.n[0], "order": prob.order,
+                       "form": "fp64", "riemann": "hllc", "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (state 671 MB, modes 13.7 GB per step)",
+                       "l1_vs_oracle_one_step": parity},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64, "unit": "TFLOP/s",
+                         "frac": achieved / PEAK_FP64, "traffic": traffic,
+                         "kernel": "predictor (k_predict_fact<double>)",
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                         "algorithmic_flops_per_launch": flops_pred, "avg_launch_ms": avg_pred},
+            "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
+            "clocks": clocks,
+            "e2e": {"value": world * zones * e2e_steps / (e2e_ms * 1e-3), "unit": "zone-updates/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": gpu_launches,
+            "cpu_baseline": cpu,
+            "forms": forms,
+        }
+        print(json.dumps(line))
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle as the reference arm: each step is one oracle step of the
+    same workload on a bounded sample (a periodic 24^3 Taylor-Green grid,
+    order 4, FP64, HLLC), on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2211_13295_gb300 import problems as P
+    small = P.tgv3d(n=24, order=4, cfl=0.3)
+    U = small.initial_state()
+    orc = oracle.Oracle(small)
+    dt = orc.cfl_dt(U, small.cfl)
+    t = 0.0
+    for _ in range(args.warmup):
+        U, smax, _ = orc.step(U, t, dt)
+        t += dt
+        dt = small.cfl / smax
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, smax, _ = orc.step(U, t, dt)
+        t += dt
+        dt = small.cfl / smax
+    el = time.perf_counter() - t0
+    value = small.zones * args.steps / el
+    line = {
+        "impl": "reference",
+        "metric": "zone-updates/sec per full ADER-WENO step at stated L1 error vs FP64 oracle",
+        "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(workload(args.n)), "sample": "tgv3d 24^3 order 4 per step"},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "tgv3d 24^3 order 4 FP64, one oracle step per bench step"},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * awe.h -- C ABI of the GB300 ADER-WENO zone update for the compressible
+ * Euler equations (libawe.so, sm_103a).
+ *
+ * The library performs the per-zone space-time update of the paper's CFD
+ * code (Subramanian, Balsara, Bhoriya, Kumar, "Techniques, Tricks and
+ * Algorithms for Efficient GPU-Based Processing of Higher Order Hyperbolic
+ * PDEs", Sec. II.2, Figs. 1-7): WENO reconstruction of the conserved
+ * variables into modal polynomials (Limiter, Fig. 3), an ADER predictor that
+ * extends them in time (Predictor, Fig. 4), HLLC Riemann fluxes at
+ * space-time quadrature points of every face (Make_Flux_X/Y/Z, Fig. 5), the
+ * conservative update (Make_dU_dt, Fig. 6) and the CFL reduction of the next
+ * time step (Update_U_Timestep, Fig. 7).  The state stays resident in device
+ * memory between steps (the paper's U_skinny lesson, Sec. II.2, Tables I-II);
+ * it crosses to the host only through awe_set_state / awe_get_state.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an awe_status (0 = AWE_OK); nothing aborts or throws
+ *    across the ABI.  awe_last_error() gives a message for the last failure
+ *    of a handle (valid until the next call on it).
+ *  - All device work runs on the CUDA stream given to awe_create (NULL = the
+ *    legacy default stream).  Calls that return host scalars synchronise that
+ *    stream before returning; the others only enqueue work.
+ *  - The library owns all of its device memory (allocated in awe_create,
+ *    freed in awe_destroy).  Caller buffers are only read or written during
+ *    the call; the library never keeps a caller pointer.
+ *  - State layout: conserved variables (rho, rho*v_x, rho*v_y[, rho*v_z], E),
+ *    FP64, structure of arrays [var][z][y][x], x fastest, active zones only
+ *    (no ghosts); nvar = dim + 2; in 2D the z extent is 1.
+ *  - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef AWE_H
+#define AWE_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct awe_grid awe_grid;
+
+typedef enum {
+  AWE_OK = 0,
+  AWE_ERR_ARG = -1,          /* invalid argument or configuration */
+  AWE_ERR_CUDA = -2,         /* a CUDA call failed (message in awe_last_error) */
+  AWE_ERR_OOM = -3,          /* device allocation failed */
+  AWE_ERR_NONPHYSICAL = -4,  /* the updated state has rho<=0, p<=0 or a non-finite value */
+  AWE_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  AWE_ERR_STATE = -6         /* call out of order (e.g. gate used without weights) */
+} awe_status;
+
+/* Boundary conditions, per face (x-low, x-high, y-low, y-high, z-low, z-high).
+ * Ghost zones are filled dimension after dimension (x, then y, then z). */
+typedef enum {
+  AWE_BC_PERIODIC = 0,
+  AWE_BC_OUTFLOW = 1,     /* copy of the nearest active zone */
+  AWE_BC_REFLECT = 2,     /* mirror image, normal momentum negated */
+  AWE_BC_INFLOW = 3,      /* fixed conserved state inflow[face] */
+  AWE_BC_DMR_BOTTOM = 4,  /* inflow[face] for x < 1/6, reflecting wall beyond */
+  AWE_BC_DMR_TOP = 5      /* inflow[face] if x < 1/6 + (1 + 20 t)/sqrt(3), else pre */
+} awe_bc;
+
+/* Arithmetic forms of the step. */
+typedef enum {
+  AWE_FP64 = 0,       /* every stage in FP64 */
+  AWE_FP32_BULK = 1   /* reconstruction, predictor and Riemann fluxes in FP32;
+                         WENO epsilon/weight path, conserved-variable update and
+                         CFL reduction in FP64 */
+} awe_prec;
+
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int n[3];              /* active zones per dimension (n[2] ignored in 2D) */
+  double lo[3], hi[3];   /* domain box (lo[2], hi[2] ignored in 2D) */
+  int order;             /* 3 or 4 (polynomial degree N = order - 1) */
+  double gamma;          /* ratio of specific heats, ideal gas */
+  int bc[6];             /* awe_bc per face */
+  double inflow[6][5];   /* conserved state per face (AWE_BC_INFLOW / DMR post-shock) */
+  double pre[5];         /* DMR pre-shock conserved state (AWE_BC_DMR_TOP) */
+  int prec;              /* awe_prec */
+  int picard;            /* predictor sweeps K (0 -> order - 1) */
+  double weno_eps;       /* WENO epsilon (absolute), e.g. 1e-12 */
+  double lin[4];         /* linear weights of the order candidate stencils */
+  double cfl;            /* CFL number used for dt_next */
+  int gate;              /* 1: reconstruct unflagged zones with linear weights
+                            (troubled-zone gate); needs awe_gate_set_weights */
+  int slab;              /* z zones per slab of the intermediate buffers
+                            (3D; 0 = whole domain in one slab) */
+} awe_config;
+
+/* Create a grid (allocates all device memory).  Cites: Fig. 1 data region.
+ * stream: a cudaStream_t (NULL = default stream).  *out receives the handle.
+ * Errors: AWE_ERR_ARG (bad config), AWE_ERR_OOM, AWE_ERR_CUDA. */
+int awe_create(const awe_config* cfg, void* stream, awe_grid** out);
+/* Destroy a grid and free its device memory (NULL is accepted). */
+int awe_destroy(awe_grid* g);
+/* Message describing the last failure on this handle ("" if none); a
+ * static string if g is NULL (last create failure). */
+const char* awe_last_error(const awe_grid* g);
+
+/* Copy a state in (on_device = 0: host pointer, 1: device pointer on this
+ * GPU) in the state layout above.  Fig. 1 "update device(U_skinny)". */
+int awe_set_state(awe_grid* g, const double* U, int on_device);
+/* Copy the state out (host or device pointer, caller owned).  Fig. 1
+ * "update host(U_skinny)".  Synchronises when on_device = 0. */
+int awe_get_state(awe_grid* g, double* U, int on_device);
+/* Simulation time t (start of the next step; used by time-dependent BCs). */
+int awe_set_time(awe_grid* g, double t);
+int awe_get_time(awe_grid* g, double* t);
+
+/* dt = cfl / max over active zones of max_d (|v_d| + c)/dx_d, FP64
+ * warp-shuffle max reduction on the current state (Eval_Tstep_Ptwise and
+ * REDUCTION(MIN:dt_next), Fig. 7).  The result also becomes the
+ * device-resident dt used by awe_step(g, 0, ...).  Synchronises if dt_out. */
+int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out);
+
+/* One full ADER-WENO step (Fig. 1 loop body): ghost zones, reconstruction,
+ * predictor, HLLC face fluxes with space-time quadrature, FP64 update, and
+ * the CFL reduction of the updated state.  dt > 0: use it; dt <= 0: use the
+ * device-resident dt (from awe_cfl_dt or the previous step) without any host
+ * round trip.  t advances by dt.  dt_next_out (may be NULL, then no
+ * synchronisation): cfg.cfl / signal-speed max of the updated state.
+ * Returns AWE_ERR_NONPHYSICAL if the updated state is not physical (the
+ * state is still updated; only reported when dt_next_out != NULL or by
+ * awe_check). */
+int awe_step(awe_grid* g, double dt, double* dt_next_out);
+/* Synchronise and report a non-physical state flagged by earlier steps. */
+int awe_check(awe_grid* g);
+
+/* ---- per-stage probes (same kernels as awe_step, for row-by-row parity) ----
+ * The box is the active zones plus one layer on each side, [-1, n_d] in each
+ * dimension.  Modes of a zone are ordered a fastest: for c in 0..N, for b in
+ * 0..N-c, for a in 0..N-b-c (c = 0 in 2D); the basis is Legendre on the zone
+ * [-1/2,1/2] with unit leading coefficient (1, xi, xi^2-1/12, xi^3-3xi/20). */
+/* Spatial modes of every box zone after reconstruction of the current state:
+ * host buffer [var][mode][box z][box y][box x], FP64 (promoted in FP32 form). */
+int awe_probe_modes(awe_grid* g, double* W);
+/* Face quadrature states of every box zone after the predictor with time step
+ * dt: host buffer [dir][side][q][var][box zone], side 0 = lower face; q =
+ * i_t1 + 2*(i_t2 + 2*i_time) (3D) or i_t1 + 2*i_time (2D), Gauss-Legendre
+ * points with 2 nodes per transverse dimension and in time. */
+int awe_probe_face_states(awe_grid* g, double dt, double* FS);
+/* Face-averaged HLLC fluxes of the active faces for time step dt: host buffer,
+ * per direction d the block [var][faces], faces (n_x + [d==0]) x (n_y +
+ * [d==1]) x (n_z + [d==2]) with x fastest, blocks concatenated over d. */
+int awe_probe_fluxes(awe_grid* g, double dt, double* F);
+
+/* ---- kernel timing (CUDA events recorded on the grid's stream) ---- */
+/* Enable (1) or disable (0) per-kernel event timing of later calls; enabling
+ * resets the counters. */
+int awe_profile(awe_grid* g, int enable);
+/* Number of kernel kinds, and per kind: name, launches and total milliseconds
+ * since timing was enabled (synchronises). */
+int awe_profile_count(void);
+int awe_profile_read(awe_grid* g, int kind, const char** name, long* launches, double* total_ms);
+/* ---- learned troubled-zone gate (not in the paper) ----
+ * Features: for each direction d and for (rho, p), the 2N undivided
+ * differences f(i+s+1) - f(i+s), s = -N..N-1, divided by |f(i)| + 1e-12,
+ * scaled by 100 and squashed by x/(1+|x|); index ((d*2+q)*2N + s+N).
+ * MLP: features -> 32 ReLU -> 32 ReLU -> logit; packed float parameters
+ * W1[32][nin], b1[32], W2[32][32], b2[32], w3[32], b3. */
+int awe_gate_dims(int dim, int order, int* nin, size_t* nparams);
+/* Copy gate parameters in (host pointer, nparams floats). */
+int awe_gate_set_weights(awe_grid* g, const float* params, size_t n);
+/* Features of every ghosted zone of the current state (zeros where the
+ * stencil does not fit): buffer [ghosted zone][nin], ghosted zones
+ * (n_x+2g) x (n_y+2g) x (n_z+2g | 1), g = order.  on_device selects the
+ * pointer kind. */
+int awe_gate_features(awe_grid* g, float* feat, int on_device);
+/* Labels of every ghosted zone (1 troubled, 0 smooth, 255 no stencil): max
+ * over directions, over rho and E, over candidates of |omega_k - lin_k| > tau
+ * for the pure-direction reconstruction of the zone means. */
+int awe_gate_labels(awe_grid* g, double tau, unsigned char* labels, int on_device);
+/* Gate flags of every ghosted zone: logit > 0 (FP32, fixed summation order)
+ * dilated over face neighbours; zones without a stencil are flagged. */
+int awe_gate_flags(awe_grid* g, unsigned char* flags, int on_device);
+/* Fraction counters of the last gated step: zones reconstructed with full
+ * WENO and total box zones. */
+int awe_gate_stats(awe_grid* g, long* flagged, long* total);
+
+/* MLP training on the GPU with the library's own forward/backward kernels.
+ * All pointers are device pointers on the current device; X [rows][nin],
+ * y [rows] in {0,1}; params/m/v hold nparams floats (Adam moments, zeroed by
+ * the caller at step 0).  Each step draws `batch` rows with a counter-based
+ * generator from (seed, step index), computes the mean logistic loss and its
+ * gradient (deterministic fixed-order reductions, no float atomics) and
+ * applies Adam (beta1 0.9, beta2 0.999, eps 1e-8, lr).  step0 is the index of
+ * the first step (for the bias correction and the row draws).  loss_out
+ * (device, may be NULL) receives the loss of each step [steps]. */
+int awe_mlp_train(int nin, float* params, float* m, float* v, const float* X, const float* y,
+                  long rows, int batch, int steps, long step0, float lr, unsigned long long seed,
+                  float* loss_out, void* stream);
+/* Mean logistic loss (FP32) and its gradient for the first B rows (device
+ * pointers; grad has nparams floats, loss one float). */
+int awe_mlp_loss_grad(int nin, const float* params, const float* X, const float* y, long B,
+                      float* grad, float* loss, void* stream);
+/* Logits of B rows in the gate's FP32 decision order (device pointers). */
+int awe_mlp_forward(int nin, const float* params, const float* X, long B, float* z, void* stream);
+
+/* ---- hardware probe ----
+ * Sustained FMA throughput of this GPU in TFLOP/s (FMA = 2 flops), FP64 and
+ * FP32, measured by a register-resident FMA kernel with CUDA events. */
+int awe_measure_fma_peaks(double* fp64_tflops, double* fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -28,7 +28,7 @@ class OraCfg(C.Structure):
         ("dim", C.c_int), ("n", C.c_int * 3), ("order", C.c_int), ("picard", C.c_int),
         ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("gamma", C.c_double),
         ("eps", C.c_double), ("lin", C.c_double * 4), ("bc", C.c_int * 6),
-        ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5),
+        ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5), ("fallback", C.c_int),
     ]
 
 
@@ -188,6 +188,7 @@ class Oracle:
         if prob.pre is not None:
             for v in range(len(prob.pre)):
                 c.pre[v] = prob.pre[v]
+        c.fallback = 1 if getattr(prob, "fallback", False) else 0
         self.cfg = c
         self.dim = prob.dim
         self.nv = prob.dim + 2
@@ -215,6 +216,17 @@ class Oracle:
         """One full step from the active state U at time t; returns
         (U_new, smax, status)."""
         Ug = self.ghosted(U, t)
+        out = np.zeros((self.nv, self.n[2], self.n[1], self.n[0]))
+        smax = C.c_double()
+        rc = lib().ora_step(C.byref(self.cfg), _dp(Ug), float(dt), _up(flags), _dp(out), C.byref(smax))
+        return out, smax.value, rc
+
+    def step_ghosted(self, Ug, dt, flags=None):
+        """One step on an array whose ghost zones are already filled (for
+        instance a window cut out of a larger ghost-filled state): returns
+        (U_new of the active zones, smax, status)."""
+        Ug = np.ascontiguousarray(Ug, dtype=np.float64)
+        assert Ug.shape == (self.nv, self.G[2], self.G[1], self.G[0]), Ug.shape
         out = np.zeros((self.nv, self.n[2], self.n[1], self.n[0]))
         smax = C.c_double()
         rc = lib().ora_step(C.byref(self.cfg), _dp(Ug), float(dt), _up(flags), _dp(out), C.byref(smax))

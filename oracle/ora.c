@@ -287,6 +287,7 @@ static void make_geom(const ora_cfg* c, geom* q) {
 static size_t gidx(const geom* q, int i, int j, int k) {
   return ((size_t)k * q->G[1] + j) * q->G[0] + i;
 }
+static int zone_physical(const geom* q, double gamma, const double* U);
 size_t ora_ghosted_size(const ora_cfg* c) {
   geom q;
   make_geom(c, &q);
@@ -713,6 +714,7 @@ int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* fla
     for (int v = 0; v < nv; ++v)
       for (int m = 0; m < ns; ++m) w[v * ns + m] = W[((size_t)v * ns + m) * nbox + bz];
     ora_predict_zone(c, w, dt, st);
+    int bad = 0;
     for (int d = 0; d < dim; ++d) {
       int t1 = -1, t2 = -1;
       for (int e = 0; e < dim; ++e)
@@ -727,10 +729,23 @@ int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* fla
           xi[t1] = xq[i1];
           if (t2 >= 0) xi[t2] = xq[i2];
           double tau = xq[it] + 0.5;
-          for (int v = 0; v < nv; ++v)
-            FS[((((size_t)d * 2 + side) * nfq + p) * nv + v) * nbox + bz] =
-                st_eval(dim, nst, stm, st + v * nst, xi, tau);
+          double U[MAXV];
+          for (int v = 0; v < nv; ++v) {
+            U[v] = st_eval(dim, nst, stm, st + v * nst, xi, tau);
+            FS[((((size_t)d * 2 + side) * nfq + p) * nv + v) * nbox + bz] = U[v];
+          }
+          if (!zone_physical(&q, c->gamma, U)) bad = 1;
         }
+    }
+    /* Positivity fallback (not in the paper; opt-in): a zone with a face
+     * state of non-positive density or pressure (or a non-finite one) falls
+     * back to first order: all its face states become the zone mean. */
+    if (c->fallback && bad) {
+      for (int d = 0; d < dim; ++d)
+        for (int side = 0; side < 2; ++side)
+          for (int p = 0; p < nfq; ++p)
+            for (int v = 0; v < nv; ++v)
+              FS[((((size_t)d * 2 + side) * nfq + p) * nv + v) * nbox + bz] = w[v * ns + 0];
     }
   }
   free(W);

@@ -41,6 +41,7 @@ typedef struct {
   int bc[6];            /* xlo, xhi, ylo, yhi, zlo, zhi */
   double inflow[6][5];  /* fixed conserved state per face (inflow / DMR post-shock) */
   double pre[5];        /* DMR pre-shock conserved state (top boundary) */
+  int fallback;         /* 1: positivity fallback of the face states (see ora.c) */
 } ora_cfg;
 
 /* ---- small building blocks (exported for the pins) ---- */

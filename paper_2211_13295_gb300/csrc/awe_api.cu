@@ -1,0 +1,621 @@
+// awe_api.cu -- C ABI of libawe.so (include/awe.h): grid lifetime, device
+// memory, the step pipeline, per-stage probes and kernel timing.
+//
+// One step (the loop body of Fig. 1):
+//   ghost zones of U_cur                                   (Boundary_Conditions)
+//   [gate: features -> MLP -> flags]                        (learned part)
+//   for each z-slab [z0, z1):
+//     recon X, Y, (Z) -> modes W of the slab box          (Limiter, Fig. 3)
+//     predictor -> face quadrature states FS               (Predictor, Fig. 4)
+//     HLLC face fluxes F                                    (Make_Flux, Fig. 5)
+//     FP64 update U_nxt = U_cur - dt div F, signal max     (Figs. 6-7)
+//   t += dt, dt_next = cfl / smax                          (device scalars)
+// The state never leaves the device between steps; dt can stay on the
+// device as well (awe_step with dt <= 0).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "awe_gate.h"
+#include "awe_internal.cuh"
+#include "awe_tables.h"
+
+namespace awe {
+cudaError_t predict_init(cudaStream_t s);
+void launch_predict_tab(const Geo& q, int prec, int picard, const void* W, const double* d_dt,
+                        int z0, int z1, const void* tab, const PTabLayout& L, void* FS,
+                        cudaStream_t s);
+}  // namespace awe
+
+using namespace awe;
+
+namespace {
+
+enum Kind { K_GHOST = 0, K_RX, K_RY, K_RZ, K_PRED, K_FLUX, K_UPD, K_GATE, K_MISC, K_COUNT };
+const char* kKindNames[K_COUNT] = {"fill_ghosts", "recon_x", "recon_y", "recon_z", "predictor",
+                                   "hllc_flux", "update_cfl", "gate", "misc"};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kinds;  // kind of interval i = (pool[2i], pool[2i+1]) ... stored as pairs
+  std::vector<std::pair<int, int>> spans;  // (event index start, event index end)
+  std::vector<int> span_kind;
+  size_t used = 0;
+  long launches[K_COUNT] = {0};
+  double ms[K_COUNT] = {0};
+};
+
+}  // namespace
+
+struct awe_grid {
+  awe_config cfg;
+  Geo q;
+  cudaStream_t s = nullptr;
+  int prec = 0, picard = 0, slab = 0;
+  double* U[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* d_scal = nullptr;  // [0] t, [1] dt, [2] saved dt
+  unsigned long long* d_smax = nullptr;
+  int* d_err = nullptr;
+  void *X = nullptr, *Y = nullptr, *XY = nullptr, *W = nullptr, *FS = nullptr, *F = nullptr;
+  double* stage = nullptr;  // state staging [nv][nact]
+  void* ptab = nullptr;
+  PTabLayout L;
+  size_t bytesT = 8;
+  awe::GateState gate;
+  std::string err;
+  Prof prof;
+};
+
+static std::string g_create_error;
+
+namespace {
+
+size_t tsize(int prec) { return prec == AWE_FP64 ? sizeof(double) : sizeof(float); }
+
+int fail(awe_grid* g, int code, const std::string& msg) {
+  if (g) g->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(awe_grid* g, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(g, e == cudaErrorMemoryAllocation ? AWE_ERR_OOM : AWE_ERR_CUDA, m);
+}
+
+#define CK(g, call)                                        \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(g, e_, #call); \
+  } while (0)
+
+// ---- profiling helpers ------------------------------------------------------
+cudaEvent_t prof_event(awe_grid* g) {
+  Prof& p = g->prof;
+  if (p.used == p.pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    p.pool.push_back(e);
+  }
+  return p.pool[p.used++];
+}
+int prof_mark(awe_grid* g) {
+  if (!g->prof.on) return -1;
+  cudaEvent_t e = prof_event(g);
+  cudaEventRecord(e, g->s);
+  return (int)g->prof.used - 1;
+}
+void prof_span(awe_grid* g, int kind, int a, int b) {
+  if (!g->prof.on || a < 0 || b < 0) return;
+  g->prof.spans.push_back({a, b});
+  g->prof.span_kind.push_back(kind);
+}
+void prof_collect(awe_grid* g) {
+  Prof& p = g->prof;
+  if (p.spans.empty()) return;
+  cudaStreamSynchronize(g->s);
+  for (size_t i = 0; i < p.spans.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.pool[p.spans[i].first], p.pool[p.spans[i].second]);
+    p.ms[p.span_kind[i]] += ms;
+    p.launches[p.span_kind[i]] += 1;
+  }
+  p.spans.clear();
+  p.span_kind.clear();
+  p.used = 0;
+}
+
+// ---- state layout kernels ----------------------------------------------------
+__global__ void k_scatter(Geo q, const double* __restrict__ src, double* __restrict__ U) {
+  long long nact = (long long)q.n[0] * q.n[1] * q.n[2];
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < nact * q.nv;
+       z += (long long)gridDim.x * blockDim.x) {
+    int v = (int)(z / nact);
+    long long a = z % nact;
+    int i = (int)(a % q.n[0]);
+    long long t = a / q.n[0];
+    int j = (int)(t % q.n[1]);
+    int k = (int)(t / q.n[1]);
+    U[v * q.ntot + gidx(q, i, j, k)] = src[z];
+  }
+}
+__global__ void k_gather(Geo q, const double* __restrict__ U, double* __restrict__ dst) {
+  long long nact = (long long)q.n[0] * q.n[1] * q.n[2];
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < nact * q.nv;
+       z += (long long)gridDim.x * blockDim.x) {
+    int v = (int)(z / nact);
+    long long a = z % nact;
+    int i = (int)(a % q.n[0]);
+    long long t = a / q.n[0];
+    int j = (int)(t % q.n[1]);
+    int k = (int)(t / q.n[1]);
+    dst[z] = U[v * q.ntot + gidx(q, i, j, k)];
+  }
+}
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < n;
+       z += (long long)gridDim.x * blockDim.x)
+    b[z] = (double)a[z];
+}
+
+long long nactive(const Geo& q) { return (long long)q.n[0] * q.n[1] * q.n[2]; }
+
+int nslabs(const awe_grid* g) {
+  if (g->q.dim == 2) return 1;
+  return (g->q.n[2] + g->slab - 1) / g->slab;
+}
+void slab_range(const awe_grid* g, int sidx, int& z0, int& z1) {
+  if (g->q.dim == 2) { z0 = 0; z1 = 1; return; }
+  z0 = sidx * g->slab;
+  z1 = z0 + g->slab < g->q.n[2] ? z0 + g->slab : g->q.n[2];
+}
+
+// sizes of the slab buffers (elements)
+struct Sizes { long long X, Y, XY, W, FS, F; };
+Sizes buffer_sizes(const Geo& q, int slab) {
+  int z1 = q.dim == 3 ? slab : 1;
+  Region rx = region_x(q, 0, z1), ry = region_y(q, 0, z1), box = region_box(q, 0, z1);
+  int NS = (int)spatial_modes(q.dim, q.N).size();
+  int NXY = q.N * (q.N - 1) / 2;
+  int NFQ = q.dim == 3 ? 8 : 4;
+  Sizes s;
+  s.X = (long long)q.nv * q.N * rx.size();
+  s.Y = q.dim == 3 ? (long long)q.nv * q.N * ry.size() : 1;
+  s.XY = q.dim == 3 ? (long long)q.nv * NXY * ry.size() : 1;
+  s.W = (long long)q.nv * NS * box.size();
+  s.FS = (long long)q.dim * 2 * NFQ * q.nv * box.size();
+  s.F = 0;
+  for (int d = 0; d < q.dim; ++d) {
+    long long e = (long long)(q.n[0] + (d == 0)) * (q.n[1] + (d == 1)) * ((q.dim == 3 ? z1 : 1) + (d == 2));
+    s.F += e * q.nv;
+  }
+  return s;
+}
+
+// the pipeline of one slab: recon, predictor, flux, (update)
+void run_slab(awe_grid* g, int z0, int z1, bool do_flux, bool do_update, const unsigned char* flags) {
+  const Geo& q = g->q;
+  int m0 = prof_mark(g);
+  cudaEvent_t evs[3];
+  cudaEvent_t* ev = nullptr;
+  int mi[3] = {-1, -1, -1};
+  if (g->prof.on) {
+    for (int k = 0; k < 3; ++k) {
+      evs[k] = prof_event(g);
+      mi[k] = (int)g->prof.used - 1;
+    }
+    ev = evs;
+  }
+  launch_recon(q, g->prec, g->U[g->cur], flags, z0, z1, g->X, g->Y, g->XY, g->W, g->s, ev);
+  prof_span(g, K_RX, m0, mi[0]);
+  prof_span(g, K_RY, mi[0], mi[1]);
+  if (q.dim == 3) prof_span(g, K_RZ, mi[1], mi[2]);
+  int last = q.dim == 3 ? mi[2] : mi[1];
+  launch_predict_tab(q, g->prec, g->picard, g->W, g->d_scal + 1, z0, z1, g->ptab, g->L, g->FS, g->s);
+  int m2 = prof_mark(g);
+  prof_span(g, K_PRED, last, m2);
+  if (!do_flux) return;
+  launch_flux(q, g->prec, g->FS, z0, z1, g->F, g->s);
+  int m3 = prof_mark(g);
+  prof_span(g, K_FLUX, m2, m3);
+  if (!do_update) return;
+  launch_update(q, g->prec, g->U[g->cur], g->F, g->d_scal + 1, z0, z1, g->U[1 - g->cur], g->d_smax,
+                g->d_err, g->s);
+  int m4 = prof_mark(g);
+  prof_span(g, K_UPD, m3, m4);
+}
+
+void fill_ghosts(awe_grid* g) {
+  int a = prof_mark(g);
+  launch_fill_ghosts(g->q, g->U[g->cur], g->d_scal + 0, g->s);
+  int b = prof_mark(g);
+  prof_span(g, K_GHOST, a, b);
+}
+
+const unsigned char* gate_flags_for_step(awe_grid* g) {
+  if (!g->cfg.gate) return nullptr;
+  int a = prof_mark(g);
+  const unsigned char* f = awe::gate_compute_flags(g->gate, g->q, g->prec, g->U[g->cur], g->s);
+  int b = prof_mark(g);
+  prof_span(g, K_GATE, a, b);
+  return f;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* awe_last_error(const awe_grid* g) {
+  return g ? g->err.c_str() : g_create_error.c_str();
+}
+
+int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
+  if (!cfg || !out) return fail(nullptr, AWE_ERR_ARG, "null argument");
+  *out = nullptr;
+  const awe_config& c = *cfg;
+  if (c.dim != 2 && c.dim != 3) return fail(nullptr, AWE_ERR_ARG, "dim must be 2 or 3");
+  if (c.order != 3 && c.order != 4) return fail(nullptr, AWE_ERR_ARG, "order must be 3 or 4");
+  if (c.prec != AWE_FP64 && c.prec != AWE_FP32_BULK) return fail(nullptr, AWE_ERR_ARG, "bad prec");
+  for (int d = 0; d < c.dim; ++d) {
+    if (c.n[d] < c.order) return fail(nullptr, AWE_ERR_ARG, "each dimension needs at least order zones");
+    if (!(c.hi[d] > c.lo[d])) return fail(nullptr, AWE_ERR_ARG, "empty domain");
+  }
+  for (int f = 0; f < 2 * c.dim; ++f)
+    if (c.bc[f] < 0 || c.bc[f] > AWE_BC_DMR_TOP) return fail(nullptr, AWE_ERR_ARG, "bad boundary condition");
+  if (!(c.gamma > 1.0)) return fail(nullptr, AWE_ERR_ARG, "gamma must exceed 1");
+  if (c.picard < 0 || c.picard > 8) return fail(nullptr, AWE_ERR_ARG, "picard out of range");
+  if (c.slab < 0) return fail(nullptr, AWE_ERR_ARG, "negative slab");
+  if (c.dim == 3 && c.n[0] * (long long)c.n[1] * c.n[2] > (1LL << 31))
+    return fail(nullptr, AWE_ERR_ARG, "grid too large");
+  const char* forced = std::getenv("AWE_FAIL_ALLOC");
+  if (forced && forced[0] == '1') return fail(nullptr, AWE_ERR_OOM, "allocation failure forced by AWE_FAIL_ALLOC");
+
+  awe_grid* g = new awe_grid();
+  g->cfg = c;
+  g->s = (cudaStream_t)stream;
+  g->prec = c.prec;
+  g->picard = c.picard > 0 ? c.picard : c.order - 1;
+  Geo& q = g->q;
+  memset(&q, 0, sizeof(q));
+  q.dim = c.dim;
+  q.N = c.order - 1;
+  q.g = c.order;
+  q.nv = c.dim + 2;
+  for (int d = 0; d < 3; ++d) {
+    bool act = d < c.dim;
+    q.n[d] = act ? c.n[d] : 1;
+    q.G[d] = act ? c.n[d] + 2 * q.g : 1;
+    q.dx[d] = act ? (c.hi[d] - c.lo[d]) / c.n[d] : 1.0;
+    q.lo[d] = act ? c.lo[d] : 0.0;
+  }
+  q.ntot = (long long)q.G[0] * q.G[1] * q.G[2];
+  q.gamma = c.gamma;
+  q.eps = c.weno_eps;
+  q.cfl = c.cfl;
+  for (int k = 0; k < 4; ++k) q.lin[k] = c.lin[k];
+  for (int f = 0; f < 6; ++f) {
+    q.bc[f] = f < 2 * c.dim ? c.bc[f] : AWE_BC_PERIODIC;
+    for (int v = 0; v < 5; ++v) q.inflow[f][v] = c.inflow[f][v];
+  }
+  for (int v = 0; v < 5; ++v) q.pre[v] = c.pre[v];
+  g->slab = (c.dim == 3 && c.slab > 0 && c.slab < c.n[2]) ? c.slab : q.n[2];
+  if (c.dim == 2) g->slab = 1;
+  g->bytesT = tsize(c.prec);
+
+  auto cleanup_fail = [&](int code) {
+    awe_destroy(g);
+    return code;
+  };
+  cudaError_t e = predict_init(g->s);
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(nullptr, e, "predictor tables");
+    delete g;
+    return rc;
+  }
+  Sizes sz = buffer_sizes(q, q.dim == 3 ? g->slab : 1);
+  size_t nbytesU = sizeof(double) * q.nv * q.ntot;
+  struct A { void** p; size_t n; const char* what; };
+  std::vector<A> allocs = {
+      {(void**)&g->U[0], nbytesU, "state"},
+      {(void**)&g->U[1], nbytesU, "state"},
+      {(void**)&g->d_scal, 4 * sizeof(double), "scalars"},
+      {(void**)&g->d_smax, sizeof(unsigned long long), "smax"},
+      {(void**)&g->d_err, sizeof(int), "err"},
+      {&g->X, g->bytesT * sz.X, "recon X fields"},
+      {&g->Y, g->bytesT * sz.Y, "recon Y fields"},
+      {&g->XY, g->bytesT * sz.XY, "recon XY fields"},
+      {&g->W, g->bytesT * sz.W, "modes"},
+      {&g->FS, g->bytesT * sz.FS, "face states"},
+      {&g->F, g->bytesT * sz.F, "fluxes"},
+      {(void**)&g->stage, sizeof(double) * q.nv * nactive(q), "staging"},
+  };
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.p, a.n);
+    if (e != cudaSuccess) {
+      std::string m = std::string("cudaMalloc ") + a.what + " (" + std::to_string(a.n) + " bytes): " + cudaGetErrorString(e);
+      g_create_error = m;
+      cudaGetLastError();
+      return cleanup_fail(AWE_ERR_OOM);
+    }
+  }
+  // node tables of the predictor in the working precision
+  g->L = ptab_layout(q.dim, q.N);
+  std::vector<double> tab = ptab_build(q.dim, q.N);
+  e = cudaMalloc(&g->ptab, g->bytesT * tab.size());
+  if (e != cudaSuccess) {
+    g_create_error = "cudaMalloc tables";
+    return cleanup_fail(AWE_ERR_OOM);
+  }
+  if (g->prec == AWE_FP64) {
+    e = cudaMemcpy(g->ptab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> tf(tab.begin(), tab.end());
+    e = cudaMemcpy(g->ptab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->U[0], 0, nbytesU, g->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->U[1], 0, nbytesU, g->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_scal, 0, 4 * sizeof(double), g->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_smax, 0, sizeof(unsigned long long), g->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("initialisation: ") + cudaGetErrorString(e);
+    return cleanup_fail(AWE_ERR_CUDA);
+  }
+  if (c.gate) {
+    int rc = awe::gate_init(g->gate, q, g->s);
+    if (rc != AWE_OK) {
+      g_create_error = "gate buffers";
+      return cleanup_fail(rc);
+    }
+  }
+  *out = g;
+  return AWE_OK;
+}
+
+int awe_destroy(awe_grid* g) {
+  if (!g) return AWE_OK;
+  cudaStreamSynchronize(g->s);
+  void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax, g->d_err, g->X, g->Y, g->XY, g->W, g->FS, g->F, g->stage, g->ptab};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  awe::gate_free(g->gate);
+  for (auto e : g->prof.pool) cudaEventDestroy(e);
+  delete g;
+  return AWE_OK;
+}
+
+int awe_set_state(awe_grid* g, const double* U, int on_device) {
+  if (!g || !U) return fail(g, AWE_ERR_ARG, "null argument");
+  const Geo& q = g->q;
+  long long n = nactive(q) * q.nv;
+  const double* src = U;
+  if (!on_device) {
+    CK(g, cudaMemcpyAsync(g->stage, U, sizeof(double) * n, cudaMemcpyHostToDevice, g->s));
+    src = g->stage;
+  }
+  int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
+  k_scatter<<<blocks, 256, 0, g->s>>>(q, src, g->U[g->cur]);
+  CK(g, cudaGetLastError());
+  if (!on_device) CK(g, cudaStreamSynchronize(g->s));
+  return AWE_OK;
+}
+
+int awe_get_state(awe_grid* g, double* U, int on_device) {
+  if (!g || !U) return fail(g, AWE_ERR_ARG, "null argument");
+  const Geo& q = g->q;
+  long long n = nactive(q) * q.nv;
+  double* dst = on_device ? U : g->stage;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
+  k_gather<<<blocks, 256, 0, g->s>>>(q, g->U[g->cur], dst);
+  CK(g, cudaGetLastError());
+  if (!on_device) {
+    CK(g, cudaMemcpyAsync(U, g->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, g->s));
+    CK(g, cudaStreamSynchronize(g->s));
+  }
+  return AWE_OK;
+}
+
+int awe_set_time(awe_grid* g, double t) {
+  if (!g) return AWE_ERR_ARG;
+  launch_set_scalar(g->d_scal + 0, t, g->s);
+  CK(g, cudaGetLastError());
+  return AWE_OK;
+}
+
+int awe_get_time(awe_grid* g, double* t) {
+  if (!g || !t) return fail(g, AWE_ERR_ARG, "null argument");
+  CK(g, cudaMemcpyAsync(t, g->d_scal + 0, sizeof(double), cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaStreamSynchronize(g->s));
+  return AWE_OK;
+}
+
+int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out) {
+  if (!g || !(cfl > 0)) return fail(g, AWE_ERR_ARG, "bad argument");
+  int a = prof_mark(g);
+  launch_signal_max(g->q, g->U[g->cur], g->d_smax, g->d_err, g->s);
+  Geo qc = g->q;
+  qc.cfl = cfl;
+  launch_finalize(qc, g->d_scal + 0, g->d_scal + 1, g->d_smax, 0, g->s);
+  int b = prof_mark(g);
+  prof_span(g, K_MISC, a, b);
+  CK(g, cudaGetLastError());
+  if (dt_out) {
+    CK(g, cudaMemcpyAsync(dt_out, g->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, g->s));
+    CK(g, cudaStreamSynchronize(g->s));
+  }
+  return AWE_OK;
+}
+
+int awe_step(awe_grid* g, double dt, double* dt_next_out) {
+  if (!g) return AWE_ERR_ARG;
+  if (g->cfg.gate && !g->gate.have_weights) return fail(g, AWE_ERR_STATE, "gate enabled without weights");
+  if (dt > 0) launch_set_scalar(g->d_scal + 1, dt, g->s);
+  fill_ghosts(g);
+  const unsigned char* flags = gate_flags_for_step(g);
+  for (int sidx = 0; sidx < nslabs(g); ++sidx) {
+    int z0, z1;
+    slab_range(g, sidx, z0, z1);
+    run_slab(g, z0, z1, true, true, flags);
+  }
+  launch_finalize(g->q, g->d_scal + 0, g->d_scal + 1, g->d_smax, 1, g->s);
+  g->cur = 1 - g->cur;
+  CK(g, cudaGetLastError());
+  if (dt_next_out) {
+    CK(g, cudaMemcpyAsync(dt_next_out, g->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, g->s));
+    return awe_check(g);
+  }
+  return AWE_OK;
+}
+
+int awe_check(awe_grid* g) {
+  if (!g) return AWE_ERR_ARG;
+  int err = 0;
+  CK(g, cudaMemcpyAsync(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaStreamSynchronize(g->s));
+  if (err) {
+    CK(g, cudaMemsetAsync(g->d_err, 0, sizeof(int), g->s));
+    return fail(g, AWE_ERR_NONPHYSICAL, "non-physical or non-finite state after the update");
+  }
+  return AWE_OK;
+}
+
+// ---- probes ------------------------------------------------------------------
+static int probe_prepare(awe_grid* g, double dt, bool set_dt) {
+  if (nslabs(g) != 1) return fail(g, AWE_ERR_STATE, "probes need a single-slab grid");
+  if (set_dt) {
+    CK(g, cudaMemcpyAsync(g->d_scal + 2, g->d_scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+    launch_set_scalar(g->d_scal + 1, dt, g->s);
+  }
+  fill_ghosts(g);
+  return AWE_OK;
+}
+static int probe_copy(awe_grid* g, const void* src, long long n, double* dst) {
+  if (g->prec == AWE_FP64) {
+    CK(g, cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, g->s));
+  } else {
+    double* tmp = nullptr;
+    CK(g, cudaMallocAsync((void**)&tmp, sizeof(double) * n, g->s));
+    k_to_double<float><<<1024, 256, 0, g->s>>>((const float*)src, tmp, n);
+    CK(g, cudaMemcpyAsync(dst, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, g->s));
+    CK(g, cudaFreeAsync(tmp, g->s));
+  }
+  CK(g, cudaStreamSynchronize(g->s));
+  return AWE_OK;
+}
+
+int awe_probe_modes(awe_grid* g, double* W) {
+  if (!g || !W) return fail(g, AWE_ERR_ARG, "null argument");
+  int rc = probe_prepare(g, 0, false);
+  if (rc) return rc;
+  const unsigned char* flags = gate_flags_for_step(g);
+  int z0, z1;
+  slab_range(g, 0, z0, z1);
+  launch_recon(g->q, g->prec, g->U[g->cur], flags, z0, z1, g->X, g->Y, g->XY, g->W, g->s, nullptr);
+  CK(g, cudaGetLastError());
+  return probe_copy(g, g->W, buffer_sizes(g->q, g->q.dim == 3 ? g->slab : 1).W, W);
+}
+
+int awe_probe_face_states(awe_grid* g, double dt, double* FS) {
+  if (!g || !FS || !(dt > 0)) return fail(g, AWE_ERR_ARG, "bad argument");
+  int rc = probe_prepare(g, dt, true);
+  if (rc) return rc;
+  const unsigned char* flags = gate_flags_for_step(g);
+  int z0, z1;
+  slab_range(g, 0, z0, z1);
+  run_slab(g, z0, z1, false, false, flags);
+  CK(g, cudaMemcpyAsync(g->d_scal + 1, g->d_scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  CK(g, cudaGetLastError());
+  return probe_copy(g, g->FS, buffer_sizes(g->q, g->q.dim == 3 ? g->slab : 1).FS, FS);
+}
+
+int awe_probe_fluxes(awe_grid* g, double dt, double* F) {
+  if (!g || !F || !(dt > 0)) return fail(g, AWE_ERR_ARG, "bad argument");
+  int rc = probe_prepare(g, dt, true);
+  if (rc) return rc;
+  const unsigned char* flags = gate_flags_for_step(g);
+  int z0, z1;
+  slab_range(g, 0, z0, z1);
+  run_slab(g, z0, z1, true, false, flags);
+  CK(g, cudaMemcpyAsync(g->d_scal + 1, g->d_scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  CK(g, cudaGetLastError());
+  return probe_copy(g, g->F, buffer_sizes(g->q, g->q.dim == 3 ? g->slab : 1).F, F);
+}
+
+// ---- profiling ---------------------------------------------------------------
+int awe_profile(awe_grid* g, int enable) {
+  if (!g) return AWE_ERR_ARG;
+  prof_collect(g);
+  g->prof.on = enable != 0;
+  if (enable)
+    for (int k = 0; k < K_COUNT; ++k) {
+      g->prof.launches[k] = 0;
+      g->prof.ms[k] = 0.0;
+    }
+  return AWE_OK;
+}
+int awe_profile_count(void) { return K_COUNT; }
+int awe_profile_read(awe_grid* g, int kind, const char** name, long* launches, double* total_ms) {
+  if (!g || kind < 0 || kind >= K_COUNT) return AWE_ERR_ARG;
+  prof_collect(g);
+  if (name) *name = kKindNames[kind];
+  if (launches) *launches = g->prof.launches[kind];
+  if (total_ms) *total_ms = g->prof.ms[kind];
+  return AWE_OK;
+}
+
+// ---- gate --------------------------------------------------------------------
+int awe_gate_set_weights(awe_grid* g, const float* params, size_t n) {
+  if (!g || !params) return fail(g, AWE_ERR_ARG, "null argument");
+  if (!g->cfg.gate) {
+    int rc = awe::gate_init(g->gate, g->q, g->s);
+    if (rc != AWE_OK) return fail(g, rc, "gate buffers");
+  }
+  int rc = awe::gate_set_weights(g->gate, g->q, params, n, g->s);
+  if (rc != AWE_OK) return fail(g, rc, "gate weights: wrong parameter count");
+  return AWE_OK;
+}
+
+int awe_gate_features(awe_grid* g, float* feat, int on_device) {
+  if (!g || !feat) return fail(g, AWE_ERR_ARG, "null argument");
+  if (!g->gate.ready) {
+    int rc = awe::gate_init(g->gate, g->q, g->s);
+    if (rc != AWE_OK) return fail(g, rc, "gate buffers");
+  }
+  fill_ghosts(g);
+  return awe::gate_features_out(g->gate, g->q, g->U[g->cur], feat, on_device, g->s);
+}
+
+int awe_gate_labels(awe_grid* g, double tau, unsigned char* labels, int on_device) {
+  if (!g || !labels) return fail(g, AWE_ERR_ARG, "null argument");
+  if (!g->gate.ready) {
+    int rc = awe::gate_init(g->gate, g->q, g->s);
+    if (rc != AWE_OK) return fail(g, rc, "gate buffers");
+  }
+  fill_ghosts(g);
+  return awe::gate_labels_out(g->gate, g->q, g->U[g->cur], tau, labels, on_device, g->s);
+}
+
+int awe_gate_flags(awe_grid* g, unsigned char* flags, int on_device) {
+  if (!g || !flags) return fail(g, AWE_ERR_ARG, "null argument");
+  if (!g->gate.have_weights) return fail(g, AWE_ERR_STATE, "gate weights not set");
+  fill_ghosts(g);
+  const unsigned char* f = awe::gate_compute_flags(g->gate, g->q, g->prec, g->U[g->cur], g->s);
+  size_t n = (size_t)g->q.ntot;
+  CK(g, cudaMemcpyAsync(flags, f, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaStreamSynchronize(g->s));
+  return AWE_OK;
+}
+
+int awe_gate_stats(awe_grid* g, long* flagged, long* total) {
+  if (!g) return AWE_ERR_ARG;
+  return awe::gate_stats(g->gate, g->q, flagged, total, g->s);
+}
+
+}  // extern "C"

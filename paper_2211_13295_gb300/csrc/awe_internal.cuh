@@ -1,0 +1,341 @@
+// awe_internal.cuh -- device-side building blocks of the ADER-WENO zone update
+// shared by the translation units of libawe.so.  Nothing here is part of the
+// C ABI (include/awe.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "../../include/awe.h"
+
+namespace awe {
+
+constexpr int kMaxV = 5;
+
+// ---------------------------------------------------------------------------
+// Grid geometry passed by value to every kernel.
+// Ghosted arrays: [var][z][y][x] with g = order ghost zones per side of every
+// active dimension; "active-relative" coordinates run from -g to n+g-1.
+// ---------------------------------------------------------------------------
+struct Geo {
+  int dim, N, g, nv;
+  int n[3];        // active zones (n[2] = 1 in 2D)
+  int G[3];        // ghosted extents (G[2] = 1 in 2D)
+  long long ntot;  // ghosted zones per variable
+  double dx[3], lo[3];
+  double gamma, eps, cfl;
+  double lin[4];
+  int bc[6];
+  double inflow[6][5];
+  double pre[5];
+};
+
+// index of an active-relative coordinate in a ghosted array
+__host__ __device__ __forceinline__ long long gidx(const Geo& q, int i, int j, int k) {
+  int gz = q.dim == 3 ? q.g : 0;
+  return ((long long)(k + gz) * q.G[1] + (j + q.g)) * q.G[0] + (i + q.g);
+}
+
+// A rectangular region of zones in active-relative coordinates, [lo, lo+ext).
+struct Region {
+  int lo[3], ext[3];
+  __host__ __device__ __forceinline__ long long size() const {
+    return (long long)ext[0] * ext[1] * ext[2];
+  }
+  __host__ __device__ __forceinline__ long long index(int i, int j, int k) const {
+    return ((long long)(k - lo[2]) * ext[1] + (j - lo[1])) * ext[0] + (i - lo[0]);
+  }
+  __host__ __device__ __forceinline__ void coords(long long r, int& i, int& j, int& k) const {
+    i = lo[0] + (int)(r % ext[0]);
+    long long t = r / ext[0];
+    j = lo[1] + (int)(t % ext[1]);
+    k = lo[2] + (int)(t / ext[1]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// mode counts
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int binom_c(int n, int k) {
+  return k == 0 ? 1 : binom_c(n - 1, k - 1) * n / k;
+}
+template <int D, int N> struct Modes {
+  static constexpr int NS = binom_c(N + D, D);          // spatial modes, degree <= N
+  static constexpr int NG = binom_c(N - 1 + D + 1, D + 1);  // space-time, degree <= N-1
+  static constexpr int NV = D + 2;
+  static constexpr int NN = N + 1;                       // predictor nodes per dimension
+  static constexpr int NSN = D == 2 ? NN * NN : NN * NN * NN;  // spatial nodes
+  static constexpr int NFQ = D == 2 ? 4 : 8;             // face quadrature points
+};
+
+// ---------------------------------------------------------------------------
+// Euler equations, ideal gas
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ T pressure_of(const T* U, T gm1) {
+  T irho = T(1) / U[0];
+  T m2 = U[1] * U[1];
+#pragma unroll
+  for (int d = 1; d < D; ++d) m2 = fma(U[1 + d], U[1 + d], m2);
+  return gm1 * (U[D + 1] - T(0.5) * m2 * irho);
+}
+
+// Physical fluxes of all D directions at one state (shared 1/rho and p).
+template <int D, typename T>
+__device__ __forceinline__ void phys_fluxes(const T* U, T gm1, T F[D][D + 2]) {
+  T irho = T(1) / U[0];
+  T v[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) v[d] = U[1 + d] * irho;
+  T m2 = U[1] * v[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) m2 = fma(U[1 + d], v[d], m2);
+  T p = gm1 * (U[D + 1] - T(0.5) * m2);
+  T Ep = U[D + 1] + p;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    F[d][0] = U[1 + d];
+#pragma unroll
+    for (int e = 0; e < D; ++e) F[d][1 + e] = U[1 + e] * v[d];
+    F[d][1 + d] += p;
+    F[d][D + 1] = Ep * v[d];
+  }
+}
+
+// HLLC flux across a face normal to direction dir (Toro, Spruce & Speares):
+// Davis-Einfeldt wave speeds with Roe averages, S* from the pressure
+// balance, left star state when S* = 0.
+template <int D, typename T>
+__device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma, T* F) {
+  const T gm1 = gamma - T(1);
+  T rl = UL[0], rr = UR[0];
+  T irl = T(1) / rl, irr = T(1) / rr;
+  T vl[D], vr[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    vl[d] = UL[1 + d] * irl;
+    vr[d] = UR[1 + d] * irr;
+  }
+  T kl = UL[1] * vl[0], kr = UR[1] * vr[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) {
+    kl = fma(UL[1 + d], vl[d], kl);
+    kr = fma(UR[1 + d], vr[d], kr);
+  }
+  T El = UL[D + 1], Er = UR[D + 1];
+  T pl = gm1 * (El - T(0.5) * kl), pr = gm1 * (Er - T(0.5) * kr);
+  T cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+  T ul = vl[dir], ur = vr[dir];
+  T sl = sqrt(rl), sr = sqrt(rr);
+  T iden = T(1) / (sl + sr);
+  T vt2 = T(0), vtn = T(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    T vt = (sl * vl[d] + sr * vr[d]) * iden;
+    vt2 = fma(vt, vt, vt2);
+    if (d == dir) vtn = vt;
+  }
+  T Ht = (sl * (El + pl) * irl + sr * (Er + pr) * irr) * iden;
+  T ct = sqrt(gm1 * (Ht - T(0.5) * vt2));
+  T SL = fmin(ul - cl, vtn - ct);
+  T SR = fmax(ur + cr, vtn + ct);
+  T ml = rl * (SL - ul), mr = rr * (SR - ur);
+  T Ss = (pr - pl + ul * ml - ur * mr) / (ml - mr);
+  // branches in the order F_L (0 <= S_L), F*_L (0 <= S*), F*_R (0 < S_R), F_R
+  if (T(0) <= SL) {
+    F[0] = UL[1 + dir];
+#pragma unroll
+    for (int e = 0; e < D; ++e) F[1 + e] = UL[1 + e] * ul;
+    F[1 + dir] += pl;
+    F[D + 1] = (El + pl) * ul;
+  } else if (!(T(0) <= Ss) && !(T(0) < SR)) {
+    F[0] = UR[1 + dir];
+#pragma unroll
+    for (int e = 0; e < D; ++e) F[1 + e] = UR[1 + e] * ur;
+    F[1 + dir] += pr;
+    F[D + 1] = (Er + pr) * ur;
+  } else {
+    const bool left = T(0) <= Ss;
+    const T* U = left ? UL : UR;
+    T S = left ? SL : SR, u = left ? ul : ur, m = left ? ml : mr, p = left ? pl : pr;
+    T rho = left ? rl : rr, E = left ? El : Er, ir = left ? irl : irr;
+    T f = m / (S - Ss);
+    // F* = F(U) + S (U* - U)
+    F[0] = U[1 + dir] + S * (f - rho);
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      T us = (e == dir) ? f * Ss : f * (U[1 + e] * ir);
+      F[1 + e] = U[1 + e] * u + S * (us - U[1 + e]);
+    }
+    F[1 + dir] += p;
+    T Es = f * (E * ir + (Ss - u) * (Ss + p / m));
+    F[D + 1] = (E + p) * u + S * (Es - E);
+  }
+}
+
+// Signal speed max_d (|v_d| + c)/dx_d of one zone (FP64), and physicality.
+template <int D>
+__device__ __forceinline__ double zone_signal(const double* U, double gamma, const double* idx_,
+                                              bool& ok) {
+  double rho = U[0];
+  double irho = 1.0 / rho;
+  double m2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) m2 = fma(U[1 + d], U[1 + d], m2);
+  double p = (gamma - 1.0) * (U[D + 1] - 0.5 * m2 * irho);
+  ok = (rho > 0.0) && (p > 0.0);
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) ok = ok && isfinite(U[v]);
+  double c = sqrt(gamma * p * irho);
+  double s = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) s = fmax(s, (fabs(U[1 + d] * irho) + c) * idx_[d]);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// WENO 1D in the "difference" form: d[j] = u(j-N) - u(0), j = 0..2N.
+// Candidates, smoothness and the final combination in T; the epsilon and
+// weight path in FP64 (product form: omega_k ~ lin_k prod_{j!=k} (eps+beta_j)^2,
+// which equals lin_k/(eps+beta_k)^2 normalised).
+// ---------------------------------------------------------------------------
+#include "stencils.inc"
+
+template <int N, typename T>
+__device__ __forceinline__ void weno_candidates(const T* d, T c[N + 1][N]) {
+  if constexpr (N == 2) weno_candidates_n2<T>(d, c);
+  else weno_candidates_n3<T>(d, c);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T weno_beta(const T* c) {
+  if constexpr (N == 2) {
+    return c[0] * c[0] + T(13.0 / 3.0) * (c[1] * c[1]);
+  } else {
+    T a = fma(T(0.1), c[2], c[0]);
+    return a * a + T(13.0 / 3.0) * (c[1] * c[1]) + T(781.0 / 20.0) * (c[2] * c[2]);
+  }
+}
+
+// Nonlinear weights (FP64) from the smoothness indicators.
+template <int N>
+__device__ __forceinline__ void weno_weights(const double* beta, const double* lin, double eps,
+                                             double* om) {
+  double s[N + 1];
+#pragma unroll
+  for (int k = 0; k <= N; ++k) {
+    double t = eps + beta[k];
+    s[k] = t * t;
+  }
+  double P[N + 1];
+  if constexpr (N == 2) {
+    P[0] = lin[0] * (s[1] * s[2]);
+    P[1] = lin[1] * (s[0] * s[2]);
+    P[2] = lin[2] * (s[0] * s[1]);
+  } else {
+    double s01 = s[0] * s[1], s23 = s[2] * s[3];
+    P[0] = lin[0] * (s[1] * s23);
+    P[1] = lin[1] * (s[0] * s23);
+    P[2] = lin[2] * (s[3] * s01);
+    P[3] = lin[3] * (s[2] * s01);
+  }
+  double sum = P[0];
+#pragma unroll
+  for (int k = 1; k <= N; ++k) sum += P[k];
+  double inv = 1.0 / sum;
+#pragma unroll
+  for (int k = 0; k <= N; ++k) om[k] = P[k] * inv;
+}
+
+// Full 1D WENO: modal coefficients out[0..N-1] of modes 1..N.
+template <int N, typename T>
+__device__ __forceinline__ void weno1d(const T* d, const double* lin, double eps, bool linear,
+                                       T* out) {
+  T c[N + 1][N];
+  weno_candidates<N, T>(d, c);
+  double om[N + 1];
+  if (linear) {
+#pragma unroll
+    for (int k = 0; k <= N; ++k) om[k] = lin[k];
+  } else {
+    double beta[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) beta[k] = (double)weno_beta<N, T>(c[k]);
+    weno_weights<N>(beta, lin, eps, om);
+  }
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    T acc = T(om[0]) * c[0][a];
+#pragma unroll
+    for (int k = 1; k <= N; ++k) acc = fma(T(om[k]), c[k][a], acc);
+    out[a] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Predictor tables (host-computed from closed forms, uploaded at create).
+// Nodes: Gauss-Legendre with NN = N+1 points on [-1/2,1/2] (space) and
+// [0,1] (time); face points: 2-point Gauss-Legendre.
+// ---------------------------------------------------------------------------
+template <typename T> struct Tabs {
+  T PN[4][4];        // P_a(x_i)
+  T WPN[4][4];       // w_i P_a(x_i) / |P_a|^2
+  T QN[4][4][4];     // w_i sum_{a'=a+1}^{a+s} D[a'][a] P_a'(x_i) / |P_a'|^2  [a][s][i]
+  T IT[4][4];        // I_e(tau_t) = int_0^tau_t L_e
+  T WLT[4][4];       // w_t L_e(tau_t) / |L_e|^2
+  T PF[4][2];        // P_a at the two face points
+  T PE[4][2];        // P_a(-1/2), P_a(+1/2)
+  T ITF[4][2];       // I_e at the two face time points
+  T WF[2];           // face weights
+};
+
+// Each translation unit that reads the tables holds its own constant copy
+// (no relocatable device code); build_tabs (awe_tables.cu) fills host copies
+// and UPLOAD_LOCAL_TABLES() copies them into the calling unit's symbols.
+void build_tabs(Tabs<double>* td, Tabs<float>* tf);  // [2] each, N = 2, 3
+static __constant__ Tabs<double> c_tab_d[2];
+static __constant__ Tabs<float> c_tab_f[2];
+template <typename T> __device__ __forceinline__ const Tabs<T>& tabs(int N);
+template <> __device__ __forceinline__ const Tabs<double>& tabs<double>(int N) { return c_tab_d[N - 2]; }
+template <> __device__ __forceinline__ const Tabs<float>& tabs<float>(int N) { return c_tab_f[N - 2]; }
+static inline cudaError_t upload_local_tables(cudaStream_t s) {
+  Tabs<double> td[2];
+  Tabs<float> tf[2];
+  build_tabs(td, tf);
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_tab_d, td, sizeof(td), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tab_f, tf, sizeof(tf), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one per stage), defined in the stage files.
+// ---------------------------------------------------------------------------
+struct Bufs;  // defined in awe_api.cu
+
+
+void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, cudaStream_t s);
+void launch_set_scalar(double* p, double v, cudaStream_t s);
+void launch_signal_max(const Geo& q, const double* U, unsigned long long* smax, int* err,
+                       cudaStream_t s);
+void launch_finalize(const Geo& q, double* d_t, double* d_dt, unsigned long long* smax,
+                     int advance, cudaStream_t s);
+
+// reconstruction passes; fields in T (double or float)
+void launch_recon(const Geo& q, int prec, const double* U, const unsigned char* flags, int z0,
+                  int z1, void* X, void* Y, void* XY, void* W, cudaStream_t s,
+                  cudaEvent_t* ev /* 3 events or nullptr */);
+void launch_predict(const Geo& q, int prec, int picard, const void* W, const double* d_dt,
+                    int z0, int z1, void* FS, cudaStream_t s);
+void launch_flux(const Geo& q, int prec, const void* FS, int z0, int z1, void* F, cudaStream_t s);
+void launch_update(const Geo& q, int prec, const double* Uold, const void* F, const double* d_dt,
+                   int z0, int z1, double* Unew, unsigned long long* smax, int* err,
+                   cudaStream_t s);
+
+// regions of the reconstruction passes for the slab [z0, z1)
+Region region_x(const Geo& q, int z0, int z1);
+Region region_y(const Geo& q, int z0, int z1);
+Region region_box(const Geo& q, int z0, int z1);
+
+}  // namespace awe

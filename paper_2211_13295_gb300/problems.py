@@ -50,6 +50,7 @@ class Problem:
     lin: tuple = ()
     picard: int = 0
     seed: Optional[int] = None
+    fallback: bool = False               # opt-in positivity fallback of the face states
     params: dict = dataclasses.field(default_factory=dict)
 
     def __post_init__(self):
