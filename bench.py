@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"],
+                    help="arithmetic form of the headline line (fp64 is the workload's)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-bulk form line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     return ap.parse_args()
@@ -229,7 +231,7 @@ def run_native(args, rank, world, local):
     torch.cuda.set_device(local)
     prob = workload(args.n)
     Uh = gpu_state(prob)
-    grid = awe.Grid(prob, prec="fp64")
+    grid = awe.Grid(prob, prec=args.form)
     grid.set_state(Uh.numpy())
     # one explicit step from the initial state for the stated error
     dt0 = grid.cfl_dt()
@@ -266,7 +268,7 @@ def run_native(args, rank, world, local):
     grid.close()
 
     forms = {}
-    if not args.no_forms:
+    if not args.no_forms and args.form == "fp64":
         g32 = awe.Grid(prob, prec="fp32")
         g32.set_state(Uh.numpy())
         dtf = g32.cfl_dt()
@@ -292,6 +294,7 @@ def run_native(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, parity = cpu_baseline_and_parity(prob, U1, Uh.numpy(), dt0)
 
+    peak = PEAK_FP64 if args.form == "fp64" else PEAK_FP32
     if rank == 0:
         line = {
             "metric": "zone-updates/sec per full ADER-WENO step at stated L1 error vs FP64 oracle",
@@ -304,16 +307,16 @@ def run_native(args, rank, world, local):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": "f64" if args.form == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(prob), "n": prob.n[0], "order": prob.order,
-                       "form": "fp64", "riemann": "hllc", "parallelism": f"replicas{world}",
+                       "form": args.form, "riemann": "hllc", "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (state 671 MB, modes 13.7 GB per step)",
                        "l1_vs_oracle_one_step": parity},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64, "unit": "TFLOP/s",
-                         "frac": achieved / PEAK_FP64, "traffic": traffic,
-                         "kernel": "predictor (k_predict_fact<double>)",
-                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"predictor (k_predict_fact<{'double' if args.form == 'fp64' else 'float'}>)",
+                         "peak_source": f"derived: 152 SMs x {'2 FP64' if args.form == 'fp64' else '128 FP32'} FMA/clk x 2 x 2.07 GHz",
                          "algorithmic_flops_per_launch": flops_pred, "avg_launch_ms": avg_pred},
             "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
             "clocks": clocks,

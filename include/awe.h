@@ -153,9 +153,10 @@ int awe_profile(awe_grid* g, int enable);
 int awe_profile_count(void);
 int awe_profile_read(awe_grid* g, int kind, const char** name, long* launches, double* total_ms);
 /* ---- learned troubled-zone gate (not in the paper) ----
- * Features: for each direction d and for (rho, p), the 2N undivided
- * differences f(i+s+1) - f(i+s), s = -N..N-1, divided by |f(i)| + 1e-12,
- * scaled by 100 and squashed by x/(1+|x|); index ((d*2+q)*2N + s+N).
+ * Features: for each direction d and for rho and E, the 2N differences
+ * f(i+k+1-N) - f(i+k-N), k = 0..2N-1, divided by their largest magnitude
+ * (0 for constant data), then that magnitude over |f(i)| + 1e-12, times 100,
+ * squashed by x/(1+x); index (d*2+q)*(2N+1) + k; nin = dim*2*(2N+1).
  * MLP: features -> 32 ReLU -> 32 ReLU -> logit; packed float parameters
  * W1[32][nin], b1[32], W2[32][32], b2[32], w3[32], b3. */
 int awe_gate_dims(int dim, int order, int* nin, size_t* nparams);

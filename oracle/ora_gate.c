@@ -37,7 +37,7 @@ static int stencil_fits(const ggeom* q, const int* idx) {
   return 1;
 }
 
-int ora_gate_num_features(int dim, int order) { return dim * 2 * 2 * (order - 1); }
+int ora_gate_num_features(int dim, int order) { return dim * 2 * (2 * (order - 1) + 1); }
 
 /* Label of a zone: 1 when, for some direction, for density or total energy,
  * some candidate's nonlinear weight differs from its linear weight by more
@@ -71,21 +71,13 @@ int ora_weno_labels(const ora_cfg* c, const double* Ug, double tau, unsigned cha
   return 0;
 }
 
-/* pressure with a fixed operation order (no contraction) */
-static double pressure(const ggeom* q, double gamma, const double* Ug, size_t z) {
-  double rho = Ug[z];
-  double ke = 0.0;
-  for (int d = 0; d < q->dim; ++d) {
-    double m = Ug[(size_t)(1 + d) * q->ntot + z];
-    ke = ke + m * m;
-  }
-  double E = Ug[(size_t)(q->nv - 1) * q->ntot + z];
-  return (gamma - 1.0) * (E - (0.5 * ke) / rho);
-}
-
-/* Features: for each direction d, for rho and p, the 2N undivided differences
- * f(i+s+1) - f(i+s), s = -N..N-1, relative to |f(i)| + 1e-12, then squashed by
- * x -> x/(1+|x|) after scaling by 100; feature index ((d*2+qty)*2N + s+N). */
+/* Features: for each direction d and for rho and E (the quantities the
+ * labels look at), the 2N undivided differences delta_k = f(i+k+1-N) -
+ * f(i+k-N), k = 0..2N-1, divided by their largest magnitude (the shape of the
+ * stencil, which is what ratios of smoothness indicators see; 0 when the data
+ * is constant), then one magnitude feature: that largest magnitude over
+ * |f(i)| + 1e-12, scaled by 100 and squashed by x/(1+x).  Index
+ * (d*2 + q)*(2N+1) + k, with k = 2N the magnitude. */
 int ora_gate_features(const ora_cfg* c, const double* Ug, float* feat) {
   ggeom q;
   mk(c, &q);
@@ -102,20 +94,22 @@ int ora_gate_features(const ora_cfg* c, const double* Ug, float* feat) {
         }
         for (int d = 0; d < q.dim; ++d)
           for (int qty = 0; qty < 2; ++qty) {
-            double vals[2 * MAXN + 1];
+            int v = qty == 0 ? 0 : q.nv - 1;
+            double vals[2 * MAXN + 1], del[2 * MAXN];
             for (int s = -N; s <= N; ++s) {
               int m[3] = {i, j, k};
               m[d] += s;
-              size_t zz = gi(&q, m[0], m[1], m[2]);
-              vals[N + s] = qty == 0 ? Ug[zz] : pressure(&q, c->gamma, Ug, zz);
+              vals[N + s] = Ug[(size_t)v * q.ntot + gi(&q, m[0], m[1], m[2])];
             }
-            double den = fabs(vals[N]) + 1e-12;
-            for (int s = -N; s < N; ++s) {
-              double r = (vals[N + s + 1] - vals[N + s]) / den;
-              double x = 100.0 * r;
-              double y = x / (1.0 + fabs(x));
-              f[(d * 2 + qty) * 2 * N + (s + N)] = (float)y;
+            double sc = 0.0;
+            for (int t = 0; t < 2 * N; ++t) {
+              del[t] = vals[t + 1] - vals[t];
+              sc = fmax(sc, fabs(del[t]));
             }
+            float* o = f + (d * 2 + qty) * (2 * N + 1);
+            for (int t = 0; t < 2 * N; ++t) o[t] = sc > 0.0 ? (float)(del[t] / sc) : 0.0f;
+            double x = 100.0 * (sc / (fabs(vals[N]) + 1e-12));
+            o[2 * N] = (float)(x / (1.0 + x));
           }
       }
   return 0;

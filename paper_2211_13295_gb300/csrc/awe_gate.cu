@@ -19,19 +19,11 @@ namespace awe {
 // ---------------------------------------------------------------------------
 // features
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double pressure_rn(const Geo& q, const double* U, long long z) {
-  double rho = U[z];
-  double ke = 0.0;
-  for (int d = 0; d < q.dim; ++d) {
-    double m = U[(1 + d) * q.ntot + z];
-    ke = __dadd_rn(ke, __dmul_rn(m, m));
-  }
-  double E = U[(q.nv - 1) * q.ntot + z];
-  return __dmul_rn(q.gamma - 1.0, __dsub_rn(E, __ddiv_rn(__dmul_rn(0.5, ke), rho)));
-}
-
-// zone z (ghosted linear index, coordinates gi,gj,gk) -> nin features; false
-// when the stencil does not fit
+// zone (gi,gj,gk) of the ghosted grid -> nin features; false when the
+// stencil does not fit.  For each direction and for rho and E: the 2N
+// differences across the stencil over their largest magnitude (the stencil's
+// shape), then that magnitude over |f(i)| + 1e-12, times 100, squashed by
+// x/(1+x).  Explicitly rounded FP64 operations in a fixed order.
 template <int D, int N>
 __device__ __forceinline__ bool zone_features(const Geo& q, const double* U, int gi, int gj, int gk,
                                               float* f) {
@@ -46,20 +38,21 @@ __device__ __forceinline__ bool zone_features(const Geo& q, const double* U, int
   for (int d = 0; d < D; ++d)
 #pragma unroll
     for (int qty = 0; qty < 2; ++qty) {
-      double vals[2 * N + 1];
+      const double* u = U + (qty == 0 ? 0 : (long long)(q.nv - 1) * q.ntot) + z;
+      double vals[2 * N + 1], del[2 * N];
 #pragma unroll
-      for (int s = -N; s <= N; ++s) {
-        long long zz = z + s * stride[d];
-        vals[N + s] = qty == 0 ? U[zz] : pressure_rn(q, U, zz);
-      }
-      double den = __dadd_rn(fabs(vals[N]), 1e-12);
+      for (int s = -N; s <= N; ++s) vals[N + s] = u[s * stride[d]];
+      double sc = 0.0;
 #pragma unroll
-      for (int s = -N; s < N; ++s) {
-        double r = __ddiv_rn(__dsub_rn(vals[N + s + 1], vals[N + s]), den);
-        double x = __dmul_rn(100.0, r);
-        double y = __ddiv_rn(x, __dadd_rn(1.0, fabs(x)));
-        f[(d * 2 + qty) * 2 * N + (s + N)] = __double2float_rn(y);
+      for (int t = 0; t < 2 * N; ++t) {
+        del[t] = __dsub_rn(vals[t + 1], vals[t]);
+        sc = fmax(sc, fabs(del[t]));
       }
+      float* o = f + (d * 2 + qty) * (2 * N + 1);
+#pragma unroll
+      for (int t = 0; t < 2 * N; ++t) o[t] = sc > 0.0 ? __double2float_rn(__ddiv_rn(del[t], sc)) : 0.0f;
+      double x = __dmul_rn(100.0, __ddiv_rn(sc, __dadd_rn(fabs(vals[N]), 1e-12)));
+      o[2 * N] = __double2float_rn(__ddiv_rn(x, __dadd_rn(1.0, x)));
     }
   return true;
 }
@@ -98,7 +91,7 @@ template <int D, int N>
 __global__ void __launch_bounds__(128) k_gate_raw(Geo q, const double* __restrict__ U,
                                                   const float* __restrict__ params, int np,
                                                   unsigned char* __restrict__ raw) {
-  constexpr int NIN = D * 2 * 2 * N;
+  constexpr int NIN = D * 2 * (2 * N + 1);
   extern __shared__ float sP[];
   for (int i = threadIdx.x; i < np; i += blockDim.x) sP[i] = params[i];
   __syncthreads();
@@ -138,7 +131,7 @@ __global__ void k_gate_dilate(Geo q, const unsigned char* __restrict__ raw,
 
 template <int D, int N>
 __global__ void k_gate_features(Geo q, const double* __restrict__ U, float* __restrict__ out) {
-  constexpr int NIN = D * 2 * 2 * N;
+  constexpr int NIN = D * 2 * (2 * N + 1);
   for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < q.ntot;
        z += (long long)gridDim.x * blockDim.x) {
     int gi = (int)(z % q.G[0]);

@@ -23,7 +23,7 @@ struct GateState {
   long last_flagged = 0, last_total = 0;
 };
 
-__host__ __device__ inline int gate_nin(int dim, int order) { return dim * 2 * 2 * (order - 1); }
+__host__ __device__ inline int gate_nin(int dim, int order) { return dim * 2 * (2 * (order - 1) + 1); }
 __host__ __device__ inline size_t gate_np(int nin) {
   return (size_t)kGateHidden * nin + kGateHidden + (size_t)kGateHidden * kGateHidden + kGateHidden +
          kGateHidden + 1;

@@ -78,16 +78,19 @@ def test_features_by_hand():
     U = prob.initial_state()
     F = orc.features(U, 0.0)
     g, N = 3, 2
-    assert F.shape[-1] == 2 * 2 * 2 * N == 16
+    assert F.shape[-1] == 2 * 2 * (2 * N + 1) == 20
     # zone at active x index 7 (last left zone): the x-stencil spans 5..9; the
-    # jump is between 7 and 8 -> difference index s=0 (f(8)-f(7))
+    # only nonzero difference is f(8) - f(7), at k = 2
     f = F[0, g + 1, g + 7]
-    r = (0.125 - 1.0) / 1.0
-    expect = np.float32(100 * r / (1 + abs(100 * r)))
-    assert f[2] == expect  # rho, x, s = 0
-    pr = (0.1 - 1.0) / 1.0
-    assert f[2 * N + 2] == np.float32(100 * pr / (1 + abs(100 * pr)))  # p, x, s = 0
-    assert np.all(f[[0, 1, 3]] == 0) and np.all(f[2 * 2 * N:] [4:] == 0)
+    # rho: differences (0, 0, -0.875, 0) -> shape (0, 0, -1, 0); magnitude 0.875/1
+    assert list(f[0:4]) == [0.0, 0.0, -1.0, 0.0]
+    assert f[4] == np.float32(87.5 / 88.5)
+    # E = p/(gamma-1): 2.5 | 0.25 -> shape (0, 0, -1, 0); magnitude 2.25/2.5
+    assert list(f[5:9]) == [0.0, 0.0, -1.0, 0.0]
+    x = 100.0 * (2.25 / (2.5 + 1e-12))
+    assert f[9] == np.float32(x / (1 + x))
+    # y: constant data -> zeros
+    assert np.all(f[10:] == 0)
     # zones without the full stencil get zero features
     assert np.all(F[0, 0, 0] == 0)
 
