@@ -197,6 +197,29 @@ int awe_mlp_loss_grad(int nin, const float* params, const float* X, const float*
 /* Logits of B rows in the gate's FP32 decision order (device pointers). */
 int awe_mlp_forward(int nin, const float* params, const float* X, long B, float* z, void* stream);
 
+/* ---- time step without device allocation ----
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory when they need a time step (a runtime that plans
+ * all device memory ahead and forbids allocation during a step, a component
+ * under a fixed device-memory budget, a time loop that must not fail on an
+ * allocation).  Same value as awe_cfl_dt, dt = cfl / max over zones of
+ * max_d (|v_d| + c)/dx_d, for a state the caller holds:
+ *   U   device pointer, conserved variables [var][z][y][x], active zones only
+ *       (the awe_get_state layout), nvar = dim + 2, read only;
+ *   n   zone counts (dim entries), dx zone sizes (dim entries), host pointers;
+ *   dt  device pointer to one double (caller owned), written by the GPU;
+ *   stream  cudaStream_t (NULL = default stream); the call only enqueues.
+ * It allocates nothing: its scratch (one partial maximum per 4096 zones) is a
+ * fixed 512 KB array inside the library, present on every GPU that loads it
+ * until the process exits, so grids above 268,435,456 zones are rejected
+ * (AWE_ERR_ARG, message in awe_last_error(NULL)).  The first call on each
+ * device looks up that array's device address; make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  dt = 0 signals a non-physical or
+ * non-finite zone. */
+int awe_cfl_dt_noalloc(const double* U, int dim, const int* n, const double* dx, double gamma,
+                       double cfl, double* dt, void* stream);
+
 /* ---- hardware probe ----
  * Sustained FMA throughput of this GPU in TFLOP/s (FMA = 2 flops), FP64 and
  * FP32, measured by a register-resident FMA kernel with CUDA events. */

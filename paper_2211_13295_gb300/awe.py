@@ -83,6 +83,8 @@ def lib():
         "awe_mlp_loss_grad": (C.c_int, [C.c_int, vp, vp, vp, C.c_long, vp, vp, vp]),
         "awe_mlp_forward": (C.c_int, [C.c_int, vp, vp, C.c_long, vp, vp]),
         "awe_measure_fma_peaks": (C.c_int, [dp, dp]),
+        "awe_cfl_dt_noalloc": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), dp, C.c_double, C.c_double,
+                                         vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -100,6 +102,7 @@ def exported_symbols():
         "awe_probe_fluxes", "awe_profile", "awe_profile_count", "awe_profile_read", "awe_gate_dims",
         "awe_gate_set_weights", "awe_gate_features", "awe_gate_labels", "awe_gate_flags", "awe_gate_stats",
         "awe_mlp_train", "awe_mlp_loss_grad", "awe_mlp_forward", "awe_measure_fma_peaks",
+        "awe_cfl_dt_noalloc",
     ]
 
 
@@ -341,6 +344,16 @@ def measure_fma_peaks():
     a, b = C.c_double(), C.c_double()
     _check(lib().awe_measure_fma_peaks(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def cfl_dt_noalloc(U, dim, n, dx, gamma, cfl, dt_out):
+    """awe_cfl_dt_noalloc on CUDA tensors: U (state, float64, awe_get_state
+    layout) and dt_out (one float64) on the current device; enqueues only."""
+    nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    dd = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
+    rc = lib().awe_cfl_dt_noalloc(C.c_void_p(U.data_ptr()), dim, nn, dd, float(gamma), float(cfl),
+                                  C.c_void_p(dt_out.data_ptr()), _current_stream())
+    _check(rc)
 
 
 # C names at module level (same names as include/awe.h)

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libawe.so")
 SOURCES = ["awe_api.cu", "awe_bc.cu", "awe_recon.cu", "awe_predict.cu", "awe_flux.cu",
-           "awe_gate.cu", "awe_tables.cu", "awe_peaks.cu"]
+           "awe_gate.cu", "awe_tables.cu", "awe_peaks.cu", "awe_noalloc.cu"]
 HEADERS = ["awe_internal.cuh", "awe_tables.h", "awe_gate.h", "stencils.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

@@ -72,6 +72,11 @@ struct awe_grid {
 
 static std::string g_create_error;
 
+namespace awe {
+// message for awe_last_error(NULL) from entry points without a handle
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace awe
+
 namespace {
 
 size_t tsize(int prec) { return prec == AWE_FP64 ? sizeof(double) : sizeof(float); }
