@@ -85,6 +85,10 @@ typedef struct {
                             (troubled-zone gate); needs awe_gate_set_weights */
   int slab;              /* z zones per slab of the intermediate buffers
                             (3D; 0 = whole domain in one slab) */
+  int fallback;          /* 1: positivity fallback (not in the paper): a zone
+                            whose face states have rho <= 0, p <= 0 or a
+                            non-finite value uses its zone mean as every face
+                            state (first order) */
 } awe_config;
 
 /* Create a grid (allocates all device memory).  Cites: Fig. 1 data region.

@@ -38,7 +38,7 @@ class AweConfig(C.Structure):
         ("order", C.c_int), ("gamma", C.c_double), ("bc", C.c_int * 6),
         ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5), ("prec", C.c_int),
         ("picard", C.c_int), ("weno_eps", C.c_double), ("lin", C.c_double * 4), ("cfl", C.c_double),
-        ("gate", C.c_int), ("slab", C.c_int),
+        ("gate", C.c_int), ("slab", C.c_int), ("fallback", C.c_int),
     ]
 
 
@@ -158,6 +158,7 @@ def make_config(prob, prec="fp64", gate=False, slab=0, cfl=None, picard=None) ->
     c.cfl = prob.cfl if cfl is None else cfl
     c.gate = 1 if gate else 0
     c.slab = slab
+    c.fallback = 1 if getattr(prob, "fallback", False) else 0
     return c
 
 

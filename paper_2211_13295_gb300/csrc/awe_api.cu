@@ -309,6 +309,7 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
     for (int v = 0; v < 5; ++v) q.inflow[f][v] = c.inflow[f][v];
   }
   for (int v = 0; v < 5; ++v) q.pre[v] = c.pre[v];
+  q.fallback = c.fallback ? 1 : 0;
   g->slab = (c.dim == 3 && c.slab > 0 && c.slab < c.n[2]) ? c.slab : q.n[2];
   if (c.dim == 2) g->slab = 1;
   g->bytesT = tsize(c.prec);

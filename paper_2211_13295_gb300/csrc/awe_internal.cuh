@@ -29,6 +29,7 @@ struct Geo {
   int bc[6];
   double inflow[6][5];
   double pre[5];
+  int fallback;  // positivity fallback of the face states
 };
 
 // index of an active-relative coordinate in a ghosted array
@@ -172,6 +173,19 @@ __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma,
     T Es = f * (E * ir + (Ss - u) * (Ss + p / m));
     F[D + 1] = (E + p) * u + S * (Es - E);
   }
+}
+
+// rho > 0, p > 0 and every component finite (positivity fallback test)
+template <int D, typename T>
+__device__ __forceinline__ bool state_physical(const T* U, T gm1) {
+  bool ok = U[0] > T(0);
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) ok = ok && isfinite(U[v]);
+  T m2 = U[1] * U[1];
+#pragma unroll
+  for (int d = 1; d < D; ++d) m2 = fma(U[1 + d], U[1 + d], m2);
+  T p = gm1 * (U[D + 1] - T(0.5) * m2 / U[0]);
+  return ok && p > T(0);
 }
 
 // Signal speed max_d (|v_d| + c)/dx_d of one zone (FP64), and physicality.

@@ -129,17 +129,41 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
           for (int b = 0; b < NG; ++b) g[v][b] = gn[v][b];
       }
     }
-    // face quadrature states: q = w(face point) - int_0^tau G
+    // face quadrature states: q = w(face point) - int_0^tau G; with the
+    // positivity fallback, a first pass checks every face point and a zone
+    // with a non-physical one writes its mean instead
+    bool bad = false;
+    if (q.fallback) {
+      for (int row = 0; row < D * 2 * NFQ; ++row) {
+        const T* fw = FW + (long long)row * NS;
+        const T* fg = FG + (long long)row * NG;
+        T u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T acc = T(0);
+#pragma unroll
+          for (int m = 0; m < NS; ++m) acc = fma(w[v][m], fw[m], acc);
+#pragma unroll
+          for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
+          u[v] = acc;
+        }
+        bad = bad || !state_physical<D, T>(u, gm1);
+      }
+    }
     for (int row = 0; row < D * 2 * NFQ; ++row) {
       const T* fw = FW + (long long)row * NS;
       const T* fg = FG + (long long)row * NG;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         T acc = T(0);
+        if (bad) {
+          acc = w[v][0];
+        } else {
 #pragma unroll
-        for (int m = 0; m < NS; ++m) acc = fma(w[v][m], fw[m], acc);
+          for (int m = 0; m < NS; ++m) acc = fma(w[v][m], fw[m], acc);
 #pragma unroll
-        for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
+          for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
+        }
         FS[((long long)row * NV + v) * nb + r] = acc;
       }
     }
@@ -149,30 +173,32 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
 // ---------------------------------------------------------------------------
 // factorised predictor, 3D, N = 3: one warp per zone
 // ---------------------------------------------------------------------------
-// index tables (constant memory): see the stage comments
-__constant__ int8_t c_sm3[20][3];     // spatial modes degree <= 3, (a,b,c)
-__constant__ int8_t c_pair3[10][2];   // (b,c) with b+c <= 3, c outer
-__constant__ int8_t c_tri2[10][3];    // (p,q,r) with p+q+r <= 2, r outer, q, p inner
-__constant__ int8_t c_pair2[6][2];    // (p,e) with p+e <= 2, e outer
-__constant__ int8_t c_gm[15][4];      // G-modes (a,b,c,e), degree <= 2, e outermost
-__constant__ int8_t c_gidx[3][3][3][3];  // (a,b,c,e) -> G-mode index, -1 outside
-__constant__ int8_t c_tri_idx[3][3][3];  // (p,q,r) -> index in c_tri2
-__constant__ int8_t c_pair2_idx[3][3];   // (p,e) -> index in c_pair2
-__constant__ int8_t c_pair3_idx[4][4];   // (b,c) -> index in c_pair3
-__constant__ int8_t c_sm3_idx[4][4][4];  // (a,b,c) -> spatial mode index
-
 template <typename T> struct FactSmem {
   // per-zone layout (elements of T)
   static constexpr int W = 0;                  // w[5][20]
   static constexpr int WN = W + 100;           // wn[5][64]
   static constexpr int G = WN + 320;           // g[5][15]
-  static constexpr int R1 = G + 75;            // T1/T2, A/B/C, Y2 (max 1640)
+  static constexpr int R1 = G + 75;            // T1/T2, A/B/C, Y2, face values (max 1640)
   static constexpr int R2 = R1 + 1640;         // Y1 (2880), Y3 (600)
   static constexpr int SIZE = R2 + 2880;       // 5015
 };
 
+// index tables copied to shared memory once per block (lane-divergent reads
+// of constant memory are serialised; shared memory is not)
+struct FactIdx {
+  int8_t sm3[20][3], pair3[10][2], tri2[10][3], pair2[6][2], gm[15][4];
+  int8_t gidx[3][3][3][3], tri_idx[3][3][3], pair2_idx[3][3], pair3_idx[4][4], sm3_idx[4][4][4];
+};
+__constant__ FactIdx c_fidx;
+
+template <typename T>
+__device__ __forceinline__ bool state_physical5(const T* u, T gm1) {
+  return state_physical<3, T>(u, gm1);
+}
+
 template <typename T, int EMAX>
-__device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, int lane, const T lam[3]) {
+__device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const FactIdx& ix, int lane,
+                                             const T lam[3]) {
   constexpr int NPE = EMAX == 0 ? 3 : 6;     // (p,e) pairs with e <= EMAX
   constexpr int NTR = EMAX == 0 ? 6 : 10;    // (p,q,e) triples with e <= EMAX
   constexpr int NGE = EMAX == 0 ? 10 : 15;   // G-modes with e <= EMAX
@@ -180,13 +206,14 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, int lane, 
   T* Y2 = z + FactSmem<T>::R1;               // [d][v][n2][pe] (pe stride 6)
   T* Y3 = z + FactSmem<T>::R2;               // [d][v][n1][tri] (tri stride 10)
   // P1: contract the first dimension (z for d = x, y; y for d = z)
+#pragma unroll 2
   for (int it = lane; it < 3 * 5 * 16 * NPE; it += 32) {
     int pe = it % NPE;
     int rest = it / NPE;
     int n2 = rest % 16;
     int dv = rest / 16;  // d*5 + v
     int d = dv / 5;
-    int p = c_pair2[pe][0], e = c_pair2[pe][1];
+    int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
     int a0 = n2 & 3, a1 = n2 >> 2;
     T acc = T(0);
 #pragma unroll
@@ -199,17 +226,18 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, int lane, 
   }
   __syncwarp();
   // P2: contract the second dimension (y for d = x; x for d = y, z)
+#pragma unroll 2
   for (int it = lane; it < 3 * 5 * 4 * NTR; it += 32) {
     int tr = it % NTR;
     int rest = it / NTR;
     int n1 = rest % 4;
     int dv = rest / 4;
     int d = dv / 5;
-    int p = c_tri2[tr][0], qq = c_tri2[tr][1], e = c_tri2[tr][2];
+    int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
     // d = x: Y3[i][(b,c,e)] = sum_j Y2[(i,j)][(c,e)] WPN[b][j]      (p=b, qq=c)
     // d = y: Y3[j][(a,c,e)] = sum_i Y2[(i,j)][(c,e)] WPN[a][i]      (p=a, qq=c)
     // d = z: Y3[k][(a,b,e)] = sum_i Y2[(i,k)][(b,e)] WPN[a][i]      (p=a, qq=b)
-    int pe = c_pair2_idx[qq][e];
+    int pe = ix.pair2_idx[qq][e];
     T acc = T(0);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -223,17 +251,17 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, int lane, 
   for (int it = lane; it < 5 * NGE; it += 32) {
     int b = it % NGE;
     int v = it / NGE;
-    int a = c_gm[b][0], bb = c_gm[b][1], c = c_gm[b][2], e = c_gm[b][3];
+    int a = ix.gm[b][0], bb = ix.gm[b][1], c = ix.gm[b][2], e = ix.gm[b][3];
     int slack = 3 - (a + bb + c + e);
-    T acc = T(0);
-    int t0 = c_tri_idx[bb][c][e], t1 = c_tri_idx[a][c][e], t2 = c_tri_idx[a][bb][e];
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    int t0 = ix.tri_idx[bb][c][e], t1 = ix.tri_idx[a][c][e], t2 = ix.tri_idx[a][bb][e];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      acc = fma(lam[0] * Y3[((0 * 5 + v) * 4 + m) * 10 + t0], tb.QN[a][slack][m], acc);
-      acc = fma(lam[1] * Y3[((1 * 5 + v) * 4 + m) * 10 + t1], tb.QN[bb][slack][m], acc);
-      acc = fma(lam[2] * Y3[((2 * 5 + v) * 4 + m) * 10 + t2], tb.QN[c][slack][m], acc);
+      s0 = fma(Y3[((0 * 5 + v) * 4 + m) * 10 + t0], tb.QN[a][slack][m], s0);
+      s1 = fma(Y3[((1 * 5 + v) * 4 + m) * 10 + t1], tb.QN[bb][slack][m], s1);
+      s2 = fma(Y3[((2 * 5 + v) * 4 + m) * 10 + t2], tb.QN[c][slack][m], s2);
     }
-    z[FactSmem<T>::G + v * 15 + b] = acc;
+    z[FactSmem<T>::G + v * 15 + b] = fma(lam[0], s0, fma(lam[1], s1, lam[2] * s2));
   }
   if (EMAX == 0) {
     for (int it = lane; it < 5 * 5; it += 32) z[FactSmem<T>::G + (it / 5) * 15 + 10 + it % 5] = T(0);
@@ -241,18 +269,27 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, int lane, 
   __syncwarp();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T* __restrict__ W,
-                                                      const double* __restrict__ d_dt, int picard,
-                                                      const T* __restrict__ tab, PTabLayout L,
-                                                      T* __restrict__ FS) {
+template <typename T, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, const T* __restrict__ W,
+                                                           const double* __restrict__ d_dt, int picard,
+                                                           const T* __restrict__ tab, PTabLayout L,
+                                                           T* __restrict__ FS) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
+  Tabs<T>& tb = *reinterpret_cast<Tabs<T>*>(smem_raw);
+  FactIdx& ix = *reinterpret_cast<FactIdx*>(smem_raw + ((sizeof(Tabs<T>) + 15) / 16) * 16);
+  T* smem = reinterpret_cast<T*>(smem_raw + ((sizeof(Tabs<T>) + 15) / 16) * 16 + ((sizeof(FactIdx) + 15) / 16) * 16);
+  {
+    const int* src = reinterpret_cast<const int*>(&tabs<T>(3));
+    int* dst = reinterpret_cast<int*>(&tb);
+    for (int i = threadIdx.x; i < (int)(sizeof(Tabs<T>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    const int8_t* s8 = reinterpret_cast<const int8_t*>(&c_fidx);
+    int8_t* d8 = reinterpret_cast<int8_t*>(&ix);
+    for (int i = threadIdx.x; i < (int)sizeof(FactIdx); i += blockDim.x) d8[i] = s8[i];
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
   T* z = smem + wib * FactSmem<T>::SIZE;
-  const Tabs<T>& tb = tabs<T>(3);
   const long long nb = box.size();
   const double dt = *d_dt;
   T lam[3];
@@ -261,7 +298,7 @@ __global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T
   const T gm1 = (T)(q.gamma - 1.0);
   const T* FW = tab + L.fw;
   const T* FG = tab + L.fg;
-  for (long long r = (long long)blockIdx.x * wpb + wib; r < nb; r += (long long)gridDim.x * wpb) {
+  for (long long r = (long long)blockIdx.x * WPB + wib; r < nb; r += (long long)gridDim.x * WPB) {
     T* sw = z + FactSmem<T>::W;
     T* swn = z + FactSmem<T>::WN;
     T* sg = z + FactSmem<T>::G;
@@ -271,21 +308,24 @@ __global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T
     {
       T* T1 = z + FactSmem<T>::R1;        // [v][i][pair3]   200
       T* T2 = T1 + 200;                   // [v][i][j][c]    320
+#pragma unroll 2
       for (int it = lane; it < 200; it += 32) {
         int pc = it % 10, rest = it / 10, i = rest % 4, v = rest / 4;
-        int b = c_pair3[pc][0], c = c_pair3[pc][1];
+        int b = ix.pair3[pc][0], c = ix.pair3[pc][1];
         T acc = T(0);
-        for (int a = 0; a <= 3 - b - c; ++a) acc = fma(sw[v * 20 + c_sm3_idx[a][b][c]], tb.PN[a][i], acc);
+        for (int a = 0; a <= 3 - b - c; ++a) acc = fma(sw[v * 20 + ix.sm3_idx[a][b][c]], tb.PN[a][i], acc);
         T1[it] = acc;
       }
       __syncwarp();
+#pragma unroll 2
       for (int it = lane; it < 320; it += 32) {
         int c = it % 4, rest = it / 4, j = rest % 4, rest2 = rest / 4, i = rest2 % 4, v = rest2 / 4;
         T acc = T(0);
-        for (int b = 0; b <= 3 - c; ++b) acc = fma(T1[(v * 4 + i) * 10 + c_pair3_idx[b][c]], tb.PN[b][j], acc);
+        for (int b = 0; b <= 3 - c; ++b) acc = fma(T1[(v * 4 + i) * 10 + ix.pair3_idx[b][c]], tb.PN[b][j], acc);
         T2[it] = acc;
       }
       __syncwarp();
+#pragma unroll 2
       for (int it = lane; it < 320; it += 32) {
         int s = it % 64, v = it / 64;
         int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
@@ -312,40 +352,45 @@ __global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T
           for (int v = 0; v < 5; ++v) Y1[((d * 5 + v) * 64 + s) * 3 + 0] = F[d][v];
       }
       __syncwarp();
-      fact_project<T, 0>(z, tb, lane, lam);
+      fact_project<T, 0>(z, tb, ix, lane, lam);
     }
     for (int sweep = 1; sweep < picard; ++sweep) {
       T* A = z + FactSmem<T>::R1;   // [v][tri][t]        200
       T* B = A + 200;               // [v][i][pair2][t]   480
       T* C = B + 480;               // [v][i][j][c][t]    960
       // E1: A[v][(a,b,c)][t] = sum_e g[(a,b,c,e)] I_e(tau_t)
+#pragma unroll 2
       for (int it = lane; it < 200; it += 32) {
         int t = it % 4, rest = it / 4, tr = rest % 10, v = rest / 10;
-        int a = c_tri2[tr][0], b = c_tri2[tr][1], c = c_tri2[tr][2];
+        int a = ix.tri2[tr][0], b = ix.tri2[tr][1], c = ix.tri2[tr][2];
         T acc = T(0);
-        for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + c_gidx[a][b][c][e]], tb.IT[e][t], acc);
+        for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + ix.gidx[a][b][c][e]], tb.IT[e][t], acc);
         A[it] = acc;
       }
       __syncwarp();
       // E2: B[v][i][(b,c)][t] = sum_a A[(a,b,c)][t] P_a(x_i)
+#pragma unroll 2
       for (int it = lane; it < 480; it += 32) {
         int t = it % 4, rest = it / 4, pc = rest % 6, rest2 = rest / 6, i = rest2 % 4, v = rest2 / 4;
-        int b = c_pair2[pc][0], c = c_pair2[pc][1];
+        int b = ix.pair2[pc][0], c = ix.pair2[pc][1];
         T acc = T(0);
-        for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + c_tri_idx[a][b][c]) * 4 + t], tb.PN[a][i], acc);
+        for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + ix.tri_idx[a][b][c]) * 4 + t], tb.PN[a][i], acc);
         B[it] = acc;
       }
       __syncwarp();
       // E3: C[v][i][j][c][t] = sum_b B[i][(b,c)][t] P_b(y_j)
+#pragma unroll 2
       for (int it = lane; it < 960; it += 32) {
         int t = it % 4, rest = it / 4, c = rest % 3, rest2 = rest / 3, j = rest2 % 4, rest3 = rest2 / 4;
         int i = rest3 % 4, v = rest3 / 4;
         T acc = T(0);
-        for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + c_pair2_idx[b][c]) * 4 + t], tb.PN[b][j], acc);
+        for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + ix.pair2_idx[b][c]) * 4 + t], tb.PN[b][j], acc);
         C[it] = acc;
       }
       __syncwarp();
       // nodes: q = wn - sum_c C P_c(z_k); fluxes; time contraction into Y1
+      // (the time weights have compile-time indices: constant-bank operands)
+      const Tabs<T>& tc = tabs<T>(3);
       for (int s = lane; s < 64; s += 32) {
         int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
         T acc[3][5][3];
@@ -371,7 +416,7 @@ __global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T
 #pragma unroll
             for (int v = 0; v < 5; ++v)
 #pragma unroll
-              for (int e = 0; e < 3; ++e) acc[d][v][e] = fma(tb.WLT[e][t], F[d][v], acc[d][v][e]);
+              for (int e = 0; e < 3; ++e) acc[d][v][e] = fma(tc.WLT[e][t], F[d][v], acc[d][v][e]);
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d)
@@ -381,19 +426,107 @@ __global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T
             for (int e = 0; e < 3; ++e) Y1[((d * 5 + v) * 64 + s) * 3 + e] = acc[d][v][e];
       }
       __syncwarp();
-      fact_project<T, 2>(z, tb, lane, lam);
+      fact_project<T, 2>(z, tb, ix, lane, lam);
     }
-    // face states
+    // face states into shared memory.  Factorised evaluation: the time
+    // integral of G at the two face time points (shared by all directions),
+    // then per (direction, side, variable) the normal axis at +-1/2 and the two
+    // transverse axes at the face Gauss points.  Row = (d*2+side)*8 + q with
+    // q = i1 + 2*(i2 + 2*it), as the probes document.
+    T* fv = z + FactSmem<T>::R1;          // [48][5] face values
+    T* gt = fv + 240;                     // [v][it][tri] time-integrated G, 100
+    for (int it = lane; it < 100; it += 32) {
+      int tr = it % 10, rest = it / 10, tq = rest % 2, v = rest / 2;
+      int a = ix.tri2[tr][0], b = ix.tri2[tr][1], c = ix.tri2[tr][2];
+      T acc = T(0);
+      for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + ix.gidx[a][b][c][e]], tb.ITF[e][tq], acc);
+      gt[it] = acc;
+    }
+    __syncwarp();
+    if (lane < 30) {
+      const int v = lane % 5, ds = lane / 5, d = ds >> 1, side = ds & 1;
+      // axes: n = d (normal), t1 < t2 the transverse ones
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      // w part: contract the normal axis at the face, then t1, then t2
+      T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index pair3_idx[p1][p2]
+#pragma unroll 1
+      for (int pc = 0; pc < 10; ++pc) {
+        int p1 = ix.pair3[pc][0], p2 = ix.pair3[pc][1];
+        T acc = T(0);
+        for (int an = 0; an <= 3 - p1 - p2; ++an) {
+          int abc[3];
+          abc[d] = an;
+          abc[t1] = p1;
+          abc[t2] = p2;
+          acc = fma(sw[v * 20 + ix.sm3_idx[abc[0]][abc[1]][abc[2]]], tb.PE[an][side], acc);
+        }
+        wn2[pc] = acc;
+      }
+      T w3[2][4];  // [i1][p2]
+#pragma unroll
+      for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+        for (int p2 = 0; p2 < 4; ++p2) {
+          T acc = T(0);
+          for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[ix.pair3_idx[p1][p2]], tb.PF[p1][i1], acc);
+          w3[i1][p2] = acc;
+        }
+      // G part per face time point
+      T gv[2][2][2];  // [it][i1][i2]
+#pragma unroll
+      for (int tq = 0; tq < 2; ++tq) {
+        T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index pair2_idx[p1][p2]
+#pragma unroll 1
+        for (int pc = 0; pc < 6; ++pc) {
+          int p1 = ix.pair2[pc][0], p2 = ix.pair2[pc][1];
+          T acc = T(0);
+          for (int an = 0; an <= 2 - p1 - p2; ++an) {
+            int abc[3];
+            abc[d] = an;
+            abc[t1] = p1;
+            abc[t2] = p2;
+            acc = fma(gt[(v * 2 + tq) * 10 + ix.tri_idx[abc[0]][abc[1]][abc[2]]], tb.PE[an][side], acc);
+          }
+          gn2[pc] = acc;
+        }
+#pragma unroll
+        for (int i1 = 0; i1 < 2; ++i1) {
+          T g3[3];
+#pragma unroll
+          for (int p2 = 0; p2 < 3; ++p2) {
+            T acc = T(0);
+            for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[ix.pair2_idx[p1][p2]], tb.PF[p1][i1], acc);
+            g3[p2] = acc;
+          }
+#pragma unroll
+          for (int i2 = 0; i2 < 2; ++i2) {
+            T acc = T(0);
+#pragma unroll
+            for (int p2 = 0; p2 < 3; ++p2) acc = fma(g3[p2], tb.PF[p2][i2], acc);
+            gv[tq][i1][i2] = acc;
+          }
+        }
+      }
+#pragma unroll
+      for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+        for (int i2 = 0; i2 < 2; ++i2) {
+          T acc = T(0);
+#pragma unroll
+          for (int p2 = 0; p2 < 4; ++p2) acc = fma(w3[i1][p2], tb.PF[p2][i2], acc);
+#pragma unroll
+          for (int tq = 0; tq < 2; ++tq) fv[(ds * 8 + i1 + 2 * (i2 + 2 * tq)) * 5 + v] = acc - gv[tq][i1][i2];
+        }
+    }
+    __syncwarp();
+    bool bad = false;
+    if (q.fallback)
+      for (int row = lane; row < 48; row += 32) bad = bad || !state_physical5<T>(fv + row * 5, gm1);
+    bad = __any_sync(0xffffffffu, bad) && q.fallback;
+    __syncwarp();
     for (int it = lane; it < 240; it += 32) {
       int v = it % 5, row = it / 5;
-      const T* fw = FW + row * 20;
-      const T* fg = FG + row * 15;
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < 20; ++m) acc = fma(sw[v * 20 + m], fw[m], acc);
-#pragma unroll
-      for (int b = 0; b < 15; ++b) acc = fma(-sg[v * 15 + b], fg[b], acc);
-      FS[((long long)row * 5 + v) * nb + r] = acc;
+      FS[((long long)row * 5 + v) * nb + r] = bad ? sw[v * 20] : fv[row * 5 + v];
     }
     __syncwarp();
   }
@@ -403,65 +536,61 @@ __global__ void __launch_bounds__(128) k_predict_fact(Geo q, Region box, const T
 static bool g_fact_tables_ready = false;
 
 static cudaError_t upload_fact_indices(cudaStream_t s) {
-  int8_t sm3[20][3], pair3[10][2], tri2[10][3], pair2[6][2], gm[15][4];
-  int8_t gidx4[3][3][3][3], tri_idx[3][3][3], pair2_idx[3][3], pair3_idx[4][4], sm3_idx[4][4][4];
-  memset(gidx4, -1, sizeof(gidx4));
-  memset(tri_idx, -1, sizeof(tri_idx));
-  memset(pair2_idx, -1, sizeof(pair2_idx));
-  memset(pair3_idx, -1, sizeof(pair3_idx));
-  memset(sm3_idx, -1, sizeof(sm3_idx));
+  FactIdx h;
+  memset(&h, -1, sizeof(h));
   int m = 0;
   for (int c = 0; c <= 3; ++c)
     for (int b = 0; b <= 3 - c; ++b)
       for (int a = 0; a <= 3 - b - c; ++a) {
-        sm3[m][0] = a; sm3[m][1] = b; sm3[m][2] = c;
-        sm3_idx[a][b][c] = m++;
+        h.sm3[m][0] = a; h.sm3[m][1] = b; h.sm3[m][2] = c;
+        h.sm3_idx[a][b][c] = m++;
       }
   m = 0;
   for (int c = 0; c <= 3; ++c)
     for (int b = 0; b <= 3 - c; ++b) {
-      pair3[m][0] = b; pair3[m][1] = c;
-      pair3_idx[b][c] = m++;
+      h.pair3[m][0] = b; h.pair3[m][1] = c;
+      h.pair3_idx[b][c] = m++;
     }
   m = 0;
   for (int r = 0; r <= 2; ++r)
     for (int qq = 0; qq <= 2 - r; ++qq)
       for (int p = 0; p <= 2 - r - qq; ++p) {
-        tri2[m][0] = p; tri2[m][1] = qq; tri2[m][2] = r;
-        tri_idx[p][qq][r] = m++;
+        h.tri2[m][0] = p; h.tri2[m][1] = qq; h.tri2[m][2] = r;
+        h.tri_idx[p][qq][r] = m++;
       }
   m = 0;
   for (int e = 0; e <= 2; ++e)
     for (int p = 0; p <= 2 - e; ++p) {
-      pair2[m][0] = p; pair2[m][1] = e;
-      pair2_idx[p][e] = m++;
+      h.pair2[m][0] = p; h.pair2[m][1] = e;
+      h.pair2_idx[p][e] = m++;
     }
   auto g = st_modes(3, 2);
   for (int b = 0; b < 15; ++b) {
-    for (int t = 0; t < 4; ++t) gm[b][t] = (int8_t)g[b][t];
-    gidx4[g[b][0]][g[b][1]][g[b][2]][g[b][3]] = b;
+    for (int t = 0; t < 4; ++t) h.gm[b][t] = (int8_t)g[b][t];
+    h.gidx[g[b][0]][g[b][1]][g[b][2]][g[b][3]] = b;
   }
-  cudaError_t e = cudaSuccess;
-#define UP(sym, src) if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(sym, src, sizeof(src), 0, cudaMemcpyHostToDevice, s)
-  UP(c_sm3, sm3); UP(c_pair3, pair3); UP(c_tri2, tri2); UP(c_pair2, pair2); UP(c_gm, gm);
-  UP(c_gidx, gidx4); UP(c_tri_idx, tri_idx); UP(c_pair2_idx, pair2_idx); UP(c_pair3_idx, pair3_idx);
-  UP(c_sm3_idx, sm3_idx);
-#undef UP
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_fidx, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
 }
+
+template <typename T> static size_t fact_smem(int wpb) {
+  return ((sizeof(Tabs<T>) + 15) / 16) * 16 + ((sizeof(FactIdx) + 15) / 16) * 16 +
+         (size_t)wpb * FactSmem<T>::SIZE * sizeof(T);
+}
+constexpr int kFactWarpsD = 1;   // FP64: one zone per block, five blocks per SM
+constexpr int kFactWarpsF = 2;   // FP32
 
 cudaError_t predict_init(cudaStream_t s) {
   if (g_fact_tables_ready) return cudaSuccess;
   cudaError_t e = upload_local_tables(s);
   if (e == cudaSuccess) e = upload_fact_indices(s);
-  if (e == cudaSuccess) {
-    size_t smd = 4 * FactSmem<double>::SIZE * sizeof(double);
-    size_t smf = 4 * FactSmem<float>::SIZE * sizeof(float);
-    e = cudaFuncSetAttribute(k_predict_fact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_predict_fact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-  }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_predict_fact<double, kFactWarpsD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fact_smem<double>(kFactWarpsD));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_predict_fact<float, kFactWarpsF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fact_smem<float>(kFactWarpsF));
   if (e == cudaSuccess) g_fact_tables_ready = true;
   return e;
 }
@@ -472,15 +601,17 @@ void launch_predict_tab(const Geo& q, int prec, int picard, const void* W, const
   Region box = region_box(q, z0, z1);
   long long nb = box.size();
   if (q.dim == 3 && q.N == 3) {
-    const int wpb = 4;
-    long long blocks = (nb + wpb - 1) / wpb;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    if (prec == AWE_FP64)
-      k_predict_fact<double><<<(int)blocks, 32 * wpb, wpb * FactSmem<double>::SIZE * sizeof(double), s>>>(
+    if (prec == AWE_FP64) {
+      long long blocks = (nb + kFactWarpsD - 1) / kFactWarpsD;
+      if (blocks > 152LL * 256) blocks = 152LL * 256;
+      k_predict_fact<double, kFactWarpsD><<<(int)blocks, 32 * kFactWarpsD, fact_smem<double>(kFactWarpsD), s>>>(
           q, box, (const double*)W, d_dt, picard, (const double*)tab, L, (double*)FS);
-    else
-      k_predict_fact<float><<<(int)blocks, 32 * wpb, wpb * FactSmem<float>::SIZE * sizeof(float), s>>>(
+    } else {
+      long long blocks = (nb + kFactWarpsF - 1) / kFactWarpsF;
+      if (blocks > 152LL * 256) blocks = 152LL * 256;
+      k_predict_fact<float, kFactWarpsF><<<(int)blocks, 32 * kFactWarpsF, fact_smem<float>(kFactWarpsF), s>>>(
           q, box, (const float*)W, d_dt, picard, (const float*)tab, L, (float*)FS);
+    }
     return;
   }
   const int th = 128;

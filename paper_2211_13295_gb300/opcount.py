@@ -104,7 +104,10 @@ def predictor_flops(D, N, picard):
             divs += 64 * 4 * fd
             flops += 2 * (3 * 5 * 16 * 6 * 4 + 3 * 5 * 4 * 10 * 4)        # P1, P2
             flops += 5 * 15 * 3 * 4 * 3                                     # P3
-        flops += 2 * (3 * 2 * 8 * 5 * 35)                                   # face states
+        # face states (factorised): G integrated at the two face times
+        # (5 x 2 x 15 FMA), then per (variable, direction, side) the normal axis,
+        # the two transverse axes and the time points: 124 FMA + 8 adds
+        flops += 2 * 150 + 30 * (2 * 124 + 8)
         return flops, divs
     # direct kernel (awe_predict.cu::k_predict_direct)
     NS = comb(N + D, D)

@@ -306,3 +306,29 @@ def test_status_codes(awe, monkeypatch):
     with pytest.raises(awe.AweError) as ei:
         awe.Grid(prob)
     assert ei.value.code == awe.AWE_ERR_OOM
+
+
+@pytest.mark.parametrize("name", ["dmr", "blast"])
+def test_positivity_fallback_matches_the_oracle(awe, name):
+    """With the opt-in positivity fallback the double Mach reflection and the
+    blast run; both implementations send the same zones to first order."""
+    if name == "dmr":
+        prob, steps = P.dmr(nx=64, ny=16).replace(fallback=True), 8
+    else:
+        prob, steps = P.blast3d(n=10, order=4).replace(fallback=True), 3
+    U = prob.initial_state()
+    g = awe.Grid(prob)
+    g.set_state(U)
+    orc = oracle.Oracle(prob)
+    t = 0.0
+    dt = orc.cfl_dt(U, prob.cfl)
+    for k in range(steps):
+        g.step(dt)
+        U, smax, rc = orc.step(U, t, dt)
+        assert rc == 0
+        t += dt
+        dt = prob.cfl / smax
+    Ug = g.get_state()
+    for v in range(prob.nv):
+        scale = max(np.abs(U[v]).sum(), np.abs(U[0]).sum())
+        assert np.abs(Ug[v] - U[v]).sum() <= 1e-12 * steps * scale, v
