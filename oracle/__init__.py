@@ -51,6 +51,7 @@ def lib():
             "ora_beta": (C.c_double, [C.c_int, dp]),
             "ora_weno1d": (None, [C.c_int, dp, C.c_double, dp, C.c_int, dp, dp]),
             "ora_hllc": (None, [C.c_int, C.c_double, C.c_int, dp, dp, dp]),
+            "ora_mc_slope": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "ora_phys_flux": (None, [C.c_int, C.c_double, C.c_int, dp, dp]),
             "ora_ghosted_size": (C.c_size_t, [cp]),
             "ora_fill_ghosts": (C.c_int, [cp, dp, C.c_double]),
@@ -134,6 +135,10 @@ def weno1d(N, u, eps, lin, linear_only=False):
     om = np.zeros(N + 1)
     lib().ora_weno1d(N, _dp(u), eps, _dp(lin), int(linear_only), _dp(c), _dp(om))
     return c, om
+
+
+def mc_slope(a, b, cfac):
+    return lib().ora_mc_slope(float(a), float(b), float(cfac))
 
 
 def hllc(dim, gamma, direction, UL, UR):
@@ -255,7 +260,7 @@ class Oracle:
         """[dim][2][nq][nv][Bz][By][Bx]"""
         Ug = self.ghosted(U, t)
         B = self.box_shape()
-        nq = 8 if self.dim == 3 else 4
+        nq = ((self.prob.order + 1) // 2) ** self.dim
         FS = np.zeros((self.dim, 2, nq, self.nv, B[2], B[1], B[0]))
         lib().ora_face_states(C.byref(self.cfg), _dp(Ug), _up(flags), float(dt), _dp(FS))
         return FS
@@ -301,6 +306,14 @@ class Oracle:
         feat = np.zeros(Ug.shape[1:] + (nf,), dtype=np.float32)
         lib().ora_gate_features(C.byref(self.cfg), _dp(Ug), _fp(feat))
         return feat
+
+    def gate_flags_ghosted(self, Ug, params, nh=32):
+        """gate flags of an array whose ghost zones are already filled"""
+        Ug = np.ascontiguousarray(Ug, dtype=np.float64)
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        fl = np.zeros(Ug.shape[1:], dtype=np.uint8)
+        lib().ora_gate_flags(C.byref(self.cfg), _dp(Ug), nh, _fp(params), _up(fl))
+        return fl
 
     def gate_flags(self, U, t, params, nh=32):
         Ug = self.ghosted(U, t)

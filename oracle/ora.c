@@ -262,6 +262,18 @@ void ora_weno1d(int N, const double* u, double eps, const double* lin, int linea
   }
 }
 
+/* Order 2: the paper's own limiter (Fig. 3).  The slope of a zone from its
+ * two one-sided differences a = u(i+1)-u(i), b = u(i)-u(i-1) is
+ * min(|a+b|/2, cfac|a|, cfac|b|) when a and b have the same sign and 0
+ * otherwise (the listing's SIGN(0.5,a) + SIGN(0.5,b) factor, with SIGN
+ * taking the sign of its second argument and +0.5 at zero); the compression
+ * factor is 2.0 for the density and 1.5 for the other variables. */
+double ora_mc_slope(double a, double b, double cfac) {
+  double m = fmin(0.5 * fabs(a + b), fmin(cfac * fabs(a), cfac * fabs(b)));
+  double sa = a >= 0.0 ? 0.5 : -0.5, sb = b >= 0.0 ? 0.5 : -0.5;
+  return m * (sa + sb);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Grid helpers                                                             */
 /* ------------------------------------------------------------------------ */
@@ -385,7 +397,7 @@ int ora_fill_ghosts(const ora_cfg* c, double* Ug, double t) {
 /* recon along dimension d of field f at every zone whose stencil fits and whose
  * inputs are finite; out[a] (a = 0..N-1) receives coefficient of P_{a+1} */
 static void recon_field(const ora_cfg* c, const geom* q, const double* f, int d,
-                        const unsigned char* flags, double** out, int nout) {
+                        const unsigned char* flags, double** out, int nout, double cfac) {
   const int N = q->N;
 #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < q->G[2]; ++k)
@@ -405,8 +417,12 @@ static void recon_field(const ora_cfg* c, const geom* q, const double* f, int d,
         }
         if (!ok) continue;
         double coef[MAXN], om[MAXN + 1];
-        int lin_only = flags ? (flags[z] == 0) : 0;
-        ora_weno1d(N, u, c->eps, c->lin, lin_only, coef, om);
+        if (N == 1) {
+          coef[0] = ora_mc_slope(u[2] - u[1], u[1] - u[0], cfac);
+        } else {
+          int lin_only = flags ? (flags[z] == 0) : 0;
+          ora_weno1d(N, u, c->eps, c->lin, lin_only, coef, om);
+        }
         for (int a = 0; a < nout; ++a) out[a][z] = coef[a];
       }
 }
@@ -437,18 +453,19 @@ int ora_reconstruct(const ora_cfg* c, const double* Ug, const unsigned char* fla
     double* outs[MAXN];
     /* x family: pure x modes from the averages */
     for (int a = 1; a <= N; ++a) outs[a - 1] = fld[a][0][0];
-    recon_field(c, &q, fld[0][0][0], 0, flags, outs, N);
+    const double cfac = v == 0 ? 2.0 : 1.5; /* order-2 limiter compression factor */
+    recon_field(c, &q, fld[0][0][0], 0, flags, outs, N, cfac);
     /* y family: recon along y of every (a,0,0) field, keep b = 1..N-a */
     for (int a = 0; a < N; ++a) {
       for (int b = 1; b <= N - a; ++b) outs[b - 1] = fld[a][b][0];
-      recon_field(c, &q, fld[a][0][0], 1, flags, outs, N - a);
+      recon_field(c, &q, fld[a][0][0], 1, flags, outs, N - a, cfac);
     }
     /* z family: recon along z of every (a,b,0) field, keep c = 1..N-a-b */
     if (dim == 3)
       for (int b = 0; b < N; ++b)
         for (int a = 0; a < N - b; ++a) {
           for (int cc = 1; cc <= N - a - b; ++cc) outs[cc - 1] = fld[a][b][cc];
-          recon_field(c, &q, fld[a][b][0], 2, flags, outs, N - a - b);
+          recon_field(c, &q, fld[a][b][0], 2, flags, outs, N - a - b, cfac);
         }
     for (int kb = 0; kb < B[2]; ++kb)
       for (int jb = 0; jb < B[1]; ++jb)
@@ -687,11 +704,12 @@ static double st_eval(int dim, int nst, const int* stm, const double* coef, cons
 /* Face quadrature states                                                    */
 /* ------------------------------------------------------------------------ */
 /* Reading: the corrector averages the Riemann flux over the face and the time
- * step with a tensor Gauss-Legendre rule of ceil(order/2) = 2 nodes per
- * transverse dimension and in time (the paper's O2 scheme is the one-node case:
- * face centre, mid-step, Fig. 5).  Point index q = i_t1 + 2*(i_t2 + 2*i_time)
- * in 3D (t1 < t2 the transverse dimensions), q = i_t1 + 2*i_time in 2D. */
-#define NQ 2
+ * step with a tensor Gauss-Legendre rule of nq = ceil(order/2) nodes per
+ * transverse dimension and in time: 2 at orders 3 and 4, and at order 2 the
+ * paper's single mid-face, mid-step point (Fig. 5).  Point index
+ * q = i_t1 + nq*(i_t2 + nq*i_time) in 3D (t1 < t2 the transverse dimensions),
+ * q = i_t1 + nq*i_time in 2D. */
+#define NQMAX 2
 int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* flags, double dt,
                     double* FS) {
   geom q;
@@ -703,10 +721,11 @@ int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* fla
   int B[3];
   for (int d = 0; d < 3; ++d) B[d] = d < dim ? q.n[d] + 2 : 1;
   const size_t nbox = (size_t)B[0] * B[1] * B[2];
+  const int NQ = (c->order + 1) / 2;
   const int nfq = dim == 3 ? NQ * NQ * NQ : NQ * NQ;
   double* W = (double*)malloc(sizeof(double) * nv * ns * nbox);
   ora_reconstruct(c, Ug, flags, W);
-  double xq[NQ], wq[NQ];
+  double xq[NQMAX], wq[NQMAX];
   ora_gauss_legendre(NQ, xq, wq);
 #pragma omp parallel for schedule(static)
   for (long bz = 0; bz < (long)nbox; ++bz) {
@@ -762,10 +781,11 @@ int ora_fluxes(const ora_cfg* c, const double* Ug, const unsigned char* flags, d
   int B[3];
   for (int d = 0; d < 3; ++d) B[d] = d < dim ? q.n[d] + 2 : 1;
   const size_t nbox = (size_t)B[0] * B[1] * B[2];
+  const int NQ = (c->order + 1) / 2;
   const int nfq = dim == 3 ? NQ * NQ * NQ : NQ * NQ;
   double* FS = (double*)malloc(sizeof(double) * dim * 2 * nfq * nv * nbox);
   ora_face_states(c, Ug, flags, dt, FS);
-  double xq[NQ], wq[NQ];
+  double xq[NQMAX], wq[NQMAX];
   ora_gauss_legendre(NQ, xq, wq);
   size_t off = 0;
   for (int d = 0; d < dim; ++d) {

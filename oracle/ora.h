@@ -32,7 +32,8 @@ enum { ORA_BC_PERIODIC = 0, ORA_BC_OUTFLOW = 1, ORA_BC_REFLECT = 2,
 typedef struct {
   int dim;              /* 2 or 3 */
   int n[3];             /* active zones per dimension (n[2] = 1 in 2D) */
-  int order;            /* 3 or 4; polynomial degree N = order - 1 */
+  int order;            /* 2, 3 or 4; polynomial degree N = order - 1 (order 2 uses
+                           the paper's MC limiter instead of WENO) */
   int picard;           /* number of Picard sweeps K of the predictor */
   double lo[3], hi[3];  /* domain box */
   double gamma;         /* ratio of specific heats */
@@ -54,6 +55,7 @@ void ora_candidate(int N, int k, const double* u, double* coef);/* stencil k of 
 double ora_beta(int N, const double* coef);                     /* smoothness of a candidate */
 void ora_weno1d(int N, const double* u, double eps, const double* lin,
                 int linear_only, double* coef, double* omega);
+double ora_mc_slope(double a, double b, double cfac);           /* order-2 limiter, Fig. 3 */
 void ora_hllc(int dim, double gamma, int dir, const double* UL, const double* UR, double* F);
 void ora_phys_flux(int dim, double gamma, int dir, const double* U, double* F);
 

@@ -178,9 +178,9 @@ template <typename T> struct FactSmem {
   static constexpr int W = 0;                  // w[5][20]
   static constexpr int WN = W + 100;           // wn[5][64]
   static constexpr int G = WN + 320;           // g[5][15]
-  static constexpr int R1 = G + 75;            // T1/T2, A/B/C, Y2, face values (max 1640)
-  static constexpr int R2 = R1 + 1640;         // Y1 (2880), Y3 (600)
-  static constexpr int SIZE = R2 + 2880;       // 5015
+  static constexpr int R1 = G + 75;            // T1/T2, C, Y2 of one direction + Y3, face values (max 1080)
+  static constexpr int R2 = R1 + 1080;         // A/B, Y1 (2880)
+  static constexpr int SIZE = R2 + 2880;       // 4455
 };
 
 // index tables copied to shared memory once per block (lane-divergent reads
@@ -202,51 +202,52 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   constexpr int NPE = EMAX == 0 ? 3 : 6;     // (p,e) pairs with e <= EMAX
   constexpr int NTR = EMAX == 0 ? 6 : 10;    // (p,q,e) triples with e <= EMAX
   constexpr int NGE = EMAX == 0 ? 10 : 15;   // G-modes with e <= EMAX
-  T* Y1 = z + FactSmem<T>::R2;               // [d][v][s][e3]  (e3 stride 3)
-  T* Y2 = z + FactSmem<T>::R1;               // [d][v][n2][pe] (pe stride 6)
-  T* Y3 = z + FactSmem<T>::R2;               // [d][v][n1][tri] (tri stride 10)
-  // P1: contract the first dimension (z for d = x, y; y for d = z)
+  const T* Y1 = z + FactSmem<T>::R2;         // [d][v][s][e3]  (e3 stride 3)
+  T* Y2 = z + FactSmem<T>::R1;               // [v][n2][pe]    one direction (pe stride 6)
+  T* Y3 = z + FactSmem<T>::R1 + 480;         // [d][v][n1][tri] (tri stride 10)
+  // one direction at a time: P1 contracts the first dimension (z for d = x,
+  // y; y for d = z), P2 the second (y for d = x; x for d = y, z)
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
 #pragma unroll 2
-  for (int it = lane; it < 3 * 5 * 16 * NPE; it += 32) {
-    int pe = it % NPE;
-    int rest = it / NPE;
-    int n2 = rest % 16;
-    int dv = rest / 16;  // d*5 + v
-    int d = dv / 5;
-    int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
-    int a0 = n2 & 3, a1 = n2 >> 2;
-    T acc = T(0);
+    for (int it = lane; it < 5 * 16 * NPE; it += 32) {
+      int pe = it % NPE;
+      int rest = it / NPE;
+      int n2 = rest % 16;
+      int v = rest / 16;
+      int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
+      int a0 = n2 & 3, a1 = n2 >> 2;
+      T acc = T(0);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      // d < 2: n2 = (i,j), sum over k; d = 2: n2 = (i,k), sum over j
-      int s = d < 2 ? (a0 + 4 * a1 + 16 * m) : (a0 + 4 * m + 16 * a1);
-      acc = fma(Y1[(dv * 64 + s) * 3 + e], tb.WPN[p][m], acc);
+      for (int m = 0; m < 4; ++m) {
+        // d < 2: n2 = (i,j), sum over k; d = 2: n2 = (i,k), sum over j
+        int s = d < 2 ? (a0 + 4 * a1 + 16 * m) : (a0 + 4 * m + 16 * a1);
+        acc = fma(Y1[((d * 5 + v) * 64 + s) * 3 + e], tb.WPN[p][m], acc);
+      }
+      Y2[(v * 16 + n2) * 6 + pe] = acc;
     }
-    Y2[(dv * 16 + n2) * 6 + pe] = acc;
-  }
-  __syncwarp();
-  // P2: contract the second dimension (y for d = x; x for d = y, z)
+    __syncwarp();
 #pragma unroll 2
-  for (int it = lane; it < 3 * 5 * 4 * NTR; it += 32) {
-    int tr = it % NTR;
-    int rest = it / NTR;
-    int n1 = rest % 4;
-    int dv = rest / 4;
-    int d = dv / 5;
-    int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
-    // d = x: Y3[i][(b,c,e)] = sum_j Y2[(i,j)][(c,e)] WPN[b][j]      (p=b, qq=c)
-    // d = y: Y3[j][(a,c,e)] = sum_i Y2[(i,j)][(c,e)] WPN[a][i]      (p=a, qq=c)
-    // d = z: Y3[k][(a,b,e)] = sum_i Y2[(i,k)][(b,e)] WPN[a][i]      (p=a, qq=b)
-    int pe = ix.pair2_idx[qq][e];
-    T acc = T(0);
+    for (int it = lane; it < 5 * 4 * NTR; it += 32) {
+      int tr = it % NTR;
+      int rest = it / NTR;
+      int n1 = rest % 4;
+      int v = rest / 4;
+      int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
+      // d = x: Y3[i][(b,c,e)] = sum_j Y2[(i,j)][(c,e)] WPN[b][j]      (p=b, qq=c)
+      // d = y: Y3[j][(a,c,e)] = sum_i Y2[(i,j)][(c,e)] WPN[a][i]      (p=a, qq=c)
+      // d = z: Y3[k][(a,b,e)] = sum_i Y2[(i,k)][(b,e)] WPN[a][i]      (p=a, qq=b)
+      int pe = ix.pair2_idx[qq][e];
+      T acc = T(0);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      int n2 = d == 0 ? (n1 + 4 * m) : (m + 4 * n1);
-      acc = fma(Y2[(dv * 16 + n2) * 6 + pe], tb.WPN[p][m], acc);
+      for (int m = 0; m < 4; ++m) {
+        int n2 = d == 0 ? (n1 + 4 * m) : (m + 4 * n1);
+        acc = fma(Y2[(v * 16 + n2) * 6 + pe], tb.WPN[p][m], acc);
+      }
+      Y3[((d * 5 + v) * 4 + n1) * 10 + tr] = acc;
     }
-    Y3[(dv * 4 + n1) * 10 + tr] = acc;
+    __syncwarp();
   }
-  __syncwarp();
   // P3: contract the derivative dimension with the Q factors, sum over d
   for (int it = lane; it < 5 * NGE; it += 32) {
     int b = it % NGE;
@@ -355,9 +356,9 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
       fact_project<T, 0>(z, tb, ix, lane, lam);
     }
     for (int sweep = 1; sweep < picard; ++sweep) {
-      T* A = z + FactSmem<T>::R1;   // [v][tri][t]        200
-      T* B = A + 200;               // [v][i][pair2][t]   480
-      T* C = B + 480;               // [v][i][j][c][t]    960
+      T* A = z + FactSmem<T>::R2;   // [v][tri][t]        200 (dead before Y1 is written)
+      T* B = A + 200;               // [v][i][pair2][t]   480 (dead before Y1 is written)
+      T* C = z + FactSmem<T>::R1;   // [v][i][j][c][t]    960
       // E1: A[v][(a,b,c)][t] = sum_e g[(a,b,c,e)] I_e(tau_t)
 #pragma unroll 2
       for (int it = lane; it < 200; it += 32) {
@@ -578,7 +579,7 @@ template <typename T> static size_t fact_smem(int wpb) {
   return ((sizeof(Tabs<T>) + 15) / 16) * 16 + ((sizeof(FactIdx) + 15) / 16) * 16 +
          (size_t)wpb * FactSmem<T>::SIZE * sizeof(T);
 }
-constexpr int kFactWarpsD = 1;   // FP64: one zone per block, five blocks per SM
+constexpr int kFactWarpsD = 1;   // FP64: one zone per block, six blocks per SM
 constexpr int kFactWarpsF = 2;   // FP32
 
 cudaError_t predict_init(cudaStream_t s) {
@@ -591,6 +592,11 @@ cudaError_t predict_init(cudaStream_t s) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_predict_fact<float, kFactWarpsF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)fact_smem<float>(kFactWarpsF));
+  // as much shared memory as the SM has: the block count per SM is set by it
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_predict_fact<double, kFactWarpsD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_predict_fact<float, kFactWarpsF>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) g_fact_tables_ready = true;
   return e;
 }

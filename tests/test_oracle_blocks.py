@@ -293,7 +293,7 @@ def eval_st(coef, modes, xi, tau):
     return acc
 
 
-@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (3, 3), (3, 4)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (3, 2), (2, 3), (2, 4), (3, 3), (3, 4)])
 def test_predictor_advects_an_isolated_contact_exactly(dim, order):
     """Constant velocity and pressure, polynomial density of degree <= N: the
     Euler equations reduce to linear advection and the exact space-time
@@ -330,6 +330,8 @@ def test_predictor_advects_an_isolated_contact_exactly(dim, order):
         assert abs(eval_st(st[0], stm, xi, tau) - rho0(shifted)) < 1e-13
         for d in range(dim):
             assert abs(eval_st(st[1 + d], stm, xi, tau) - vel[d] * rho0(shifted)) < 1e-13
+    if N < 2:
+        return
     # with one sweep fewer the cubic/quadratic-in-time terms are missing (for N >= 2)
     prob2 = prob.replace(picard=N - 1)
     st2 = oracle.Oracle(prob2).predict_zone(w, dt)
@@ -414,3 +416,16 @@ def test_hllc_is_exact_for_an_isolated_moving_shock():
                 R[1] = -1
                 Fm = oracle.hllc(dim, G, 0, R * UR, R * UL)
                 assert np.allclose(Fm, euler_flux(R * UL, 0, dim), rtol=1e-12, atol=1e-12), (M, w, dim)
+
+
+def test_mc_limiter_of_fig3_by_hand():
+    """Fig. 3: MC_Limiter(a, b, cfac) = MIN(0.5|a+b|, cfac|a|, cfac|b|) *
+    (SIGN(0.5,a) + SIGN(0.5,b)), SIGN(A,B) = |A| with the sign of B."""
+    cases = [((1.0, 3.0, 2.0), 2.0),     # min(2, 2, 6)
+             ((3.0, 1.0, 1.5), 1.5),     # min(2, 4.5, 1.5)
+             ((-1.0, -0.25, 2.0), -0.5),  # min(0.625, 2, 0.5) negative
+             ((1.0, -1.0, 2.0), 0.0),     # opposite signs
+             ((0.0, 2.0, 2.0), 0.0),      # cfac*|a| = 0
+             ((0.4, 0.4, 1.5), 0.4)]      # smooth: the centred slope
+    for (a, b, cf), exp in cases:
+        assert oracle.mc_slope(a, b, cf) == exp, (a, b, cf)

@@ -88,8 +88,8 @@ def test_ghost_zones_dmr():
         assert np.array_equal(top, post if x < xs_t else pre)
 
 
-@pytest.mark.parametrize("dim,order,bc", [(2, 3, "periodic"), (2, 4, "outflow"), (3, 3, "periodic"),
-                                          (3, 4, "reflect")])
+@pytest.mark.parametrize("dim,order,bc", [(2, 2, "periodic"), (3, 2, "reflect"), (2, 3, "periodic"),
+                                          (2, 4, "outflow"), (3, 3, "periodic"), (3, 4, "reflect")])
 def test_free_stream_is_preserved_bitwise(dim, order, bc):
     vel = (0.3, -0.2, 0.1) if bc != "reflect" else (0.0, 0.0, 0.0)
     prob = P.uniform(dim=dim, n=6 if dim == 3 else 10, order=order, vel=vel, bc=bc)
@@ -195,7 +195,8 @@ def test_diagonal_reflection_on_an_anisotropic_grid(dim, order):
     assert np.abs(A1 - UA).max() > 1e-3
 
 
-@pytest.mark.parametrize("order,ns,t_end,min_rate", [(3, (32, 64, 128), 1.0, 2.7), (4, (16, 32, 64), 1.0, 3.7)])
+@pytest.mark.parametrize("order,ns,t_end,min_rate", [(2, (32, 64, 128), 1.0, 1.6), (3, (32, 64, 128), 1.0, 2.7),
+                                                    (4, (16, 32, 64), 1.0, 3.7)])
 def test_design_order_on_the_isentropic_vortex(order, ns, t_end, min_rate):
     errs = []
     for n in ns:
@@ -265,3 +266,24 @@ def test_lower_dimensional_consistency(order):
     for a_v, b_v in ((0, 0), (1, 3), (2, 1), (3, 4)):
         assert np.abs(B[b_v][:, 0, 0] - A[a_v][0, 0, :]).max() < 1e-13 * scale, (a_v, b_v)
     assert np.abs(B[2]).max() < 1e-15
+
+
+def test_order2_face_state_is_fig5():
+    """At order 2 the face state is the paper's U_L = U1 + U2/2 + U5/2 at the
+    face centre and mid-step (Fig. 5): U1 the zone mean, U2 the MC slope
+    (Fig. 3), U5 the coefficient of tau of the predicted polynomial."""
+    prob = P.vortex2d(n=12, order=2)
+    orc = oracle.Oracle(prob)
+    U = prob.initial_state()
+    dt = orc.cfl_dt(U, 0.4)
+    W = orc.reconstruct(U, 0.0)          # [v][mode][By][Bx]: modes 1, xi, eta
+    FS = orc.face_states(U, 0.0, dt)     # [dir][side][1][v][...]
+    for (jb, ib) in ((3, 4), (6, 2), (9, 10)):
+        w = W[:, :, 0, jb, ib]
+        st = orc.predict_zone(w.reshape(-1).copy(), dt)
+        # space-time modes (a, b, e): e outermost: (0,0,0), (1,0,0), (0,1,0), (0,0,1)
+        U5 = 2.0 * st[:, 3]              # L1 = 2 tau - 1: coefficient of tau is 2*c
+        UL = w[:, 0] + 0.5 * w[:, 1] + 0.5 * U5
+        UR = w[:, 0] - 0.5 * w[:, 1] + 0.5 * U5
+        assert np.allclose(FS[0, 1, 0, :, 0, jb, ib], UL, rtol=0, atol=1e-14)
+        assert np.allclose(FS[0, 0, 0, :, 0, jb, ib], UR, rtol=0, atol=1e-14)
