@@ -227,6 +227,24 @@ def cpu_baseline_and_parity(prob, grid_state_after, U0, dt0, n_windows=3, m=4, s
     return base, parity
 
 
+def orders_192(args, world):
+    """Zone-updates/s of the FP64 form at orders 2, 3 and 4 on a 192^3
+    Taylor-Green grid: the grid of the paper's Table II (whose A100 numbers
+    were measured on an unnamed problem; context only)."""
+    from paper_2211_13295_gb300 import awe
+    from paper_2211_13295_gb300 import problems as P
+    out = {}
+    for order in (2, 3, 4):
+        prob = P.tgv3d(n=192, order=order, cfl=0.3)
+        g = awe.Grid(prob)
+        g.set_state(prob.initial_state())
+        ms, _ = time_steps(g, 3, 3, world)
+        ms = max_over_ranks(ms, world)
+        g.close()
+        out[f"O{order}"] = world * prob.zones * 3 / (ms * 1e-3)
+    return out
+
+
 def gated_forms(args, prob, Uh, U1, zones, world):
     """Train the troubled-zone gate on the GPU (labels from the method on
     short seeded runs of the vortex, Sod, blast and Kelvin-Helmholtz
@@ -337,6 +355,10 @@ def run_native(args, rank, world, local):
     if not args.no_forms and args.form == "fp64":
         forms.update(gated_forms(args, prob, Uh, U1, zones, world))
 
+    table2 = None
+    if not args.no_forms and args.form == "fp64":
+        table2 = orders_192(args, world)
+
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -373,6 +395,7 @@ def run_native(args, rank, world, local):
             "gpu_launches": gpu_launches,
             "cpu_baseline": cpu,
             "forms": forms,
+            "orders_tgv192_fp64": table2,
         }
         print(json.dumps(line))
 

@@ -240,7 +240,7 @@ class Grid:
         return W
 
     def probe_face_states(self, dt):
-        nq = 8 if self.prob.dim == 3 else 4
+        nq = ((self.prob.order + 1) // 2) ** self.prob.dim
         FS = np.zeros((self.prob.dim, 2, nq, self.nv) + self.box_shape)
         _check(lib().awe_probe_face_states(self.h, float(dt), FS.ctypes.data_as(C.c_void_p)), self.h)
         return FS

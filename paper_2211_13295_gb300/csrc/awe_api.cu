@@ -187,11 +187,12 @@ Sizes buffer_sizes(const Geo& q, int slab) {
   Region rx = region_x(q, 0, z1), ry = region_y(q, 0, z1), box = region_box(q, 0, z1);
   int NS = (int)spatial_modes(q.dim, q.N).size();
   int NXY = q.N * (q.N - 1) / 2;
-  int NFQ = q.dim == 3 ? 8 : 4;
+  int nq = (q.N + 2) / 2;
+  int NFQ = q.dim == 3 ? nq * nq * nq : nq * nq;
   Sizes s;
   s.X = (long long)q.nv * q.N * rx.size();
   s.Y = q.dim == 3 ? (long long)q.nv * q.N * ry.size() : 1;
-  s.XY = q.dim == 3 ? (long long)q.nv * NXY * ry.size() : 1;
+  s.XY = q.dim == 3 && NXY > 0 ? (long long)q.nv * NXY * ry.size() : 1;
   s.W = (long long)q.nv * NS * box.size();
   s.FS = (long long)q.dim * 2 * NFQ * q.nv * box.size();
   s.F = 0;
@@ -265,7 +266,8 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   *out = nullptr;
   const awe_config& c = *cfg;
   if (c.dim != 2 && c.dim != 3) return fail(nullptr, AWE_ERR_ARG, "dim must be 2 or 3");
-  if (c.order != 3 && c.order != 4) return fail(nullptr, AWE_ERR_ARG, "order must be 3 or 4");
+  if (c.order < 2 || c.order > 4) return fail(nullptr, AWE_ERR_ARG, "order must be 2, 3 or 4");
+  if (c.gate && c.order == 2) return fail(nullptr, AWE_ERR_ARG, "the gate needs order 3 or 4 (WENO)");
   if (c.prec != AWE_FP64 && c.prec != AWE_FP32_BULK) return fail(nullptr, AWE_ERR_ARG, "bad prec");
   for (int d = 0; d < c.dim; ++d) {
     if (c.n[d] < c.order) return fail(nullptr, AWE_ERR_ARG, "each dimension needs at least order zones");

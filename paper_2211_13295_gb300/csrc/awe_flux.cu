@@ -19,16 +19,16 @@ __host__ __device__ __forceinline__ void face_ext(const Geo& q, int d, int z0, i
   E[2] = (q.dim == 3 ? z1 - z0 : 1) + (d == 2);
 }
 
-template <int D, typename T>
+template <int D, int N, typename T>
 __global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, int z1,
                                               const T* __restrict__ FS, T* __restrict__ F) {
-  constexpr int NV = D + 2, NFQ = Modes<D, 2>::NFQ;
+  constexpr int NV = D + 2, NFQ = Modes<D, N>::NFQ;
   int E[3];
   face_ext(q, d, z0, z1, E);
   const long long nf = (long long)E[0] * E[1] * E[2];
   const long long nb = box.size();
   const T gamma = (T)q.gamma;
-  const T wq = D == 2 ? T(0.25) : T(0.125);
+  const T wq = T(1) / T(NFQ);  // tensor Gauss weights (1/2 per 2-point dimension, 1 for 1 point)
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
        f += (long long)gridDim.x * blockDim.x) {
     int i = (int)(f % E[0]);
@@ -126,13 +126,17 @@ void launch_flux(const Geo& q, int prec, const void* FS, int z0, int z1, void* F
     face_ext(q, d, z0, z1, E);
     long long nf = (long long)E[0] * E[1] * E[2];
     int blocks = grid_for(nf, 128, 152LL * 64);
-    if (q.dim == 2) {
-      if (prec == AWE_FP64) k_flux<2, double><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const double*)FS, (double*)F + off);
-      else k_flux<2, float><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const float*)FS, (float*)F + off);
-    } else {
-      if (prec == AWE_FP64) k_flux<3, double><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const double*)FS, (double*)F + off);
-      else k_flux<3, float><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const float*)FS, (float*)F + off);
+#define AWE_FLUX(D_, N_)                                                                          \
+    if (q.dim == D_ && q.N == N_) {                                                               \
+      if (prec == AWE_FP64)                                                                       \
+        k_flux<D_, N_, double><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const double*)FS,        \
+                                                      (double*)F + off);                          \
+      else                                                                                        \
+        k_flux<D_, N_, float><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const float*)FS,          \
+                                                     (float*)F + off);                            \
     }
+    AWE_FLUX(2, 1) AWE_FLUX(2, 2) AWE_FLUX(2, 3) AWE_FLUX(3, 1) AWE_FLUX(3, 2) AWE_FLUX(3, 3)
+#undef AWE_FLUX
     off += nf * q.nv;
   }
 }

@@ -67,7 +67,8 @@ template <int D, int N> struct Modes {
   static constexpr int NV = D + 2;
   static constexpr int NN = N + 1;                       // predictor nodes per dimension
   static constexpr int NSN = D == 2 ? NN * NN : NN * NN * NN;  // spatial nodes
-  static constexpr int NFQ = D == 2 ? 4 : 8;             // face quadrature points
+  static constexpr int NQ = (N + 2) / 2;                 // face Gauss points per dimension
+  static constexpr int NFQ = D == 2 ? NQ * NQ : NQ * NQ * NQ;  // face quadrature points
 };
 
 // ---------------------------------------------------------------------------
@@ -216,6 +217,17 @@ __device__ __forceinline__ double zone_signal(const double* U, double gamma, con
 // ---------------------------------------------------------------------------
 #include "stencils.inc"
 
+// Order 2: the paper's MC limiter (Fig. 3), slope from the one-sided
+// differences a = u(i+1)-u(i), b = u(i)-u(i-1):
+// min(|a+b|/2, cfac|a|, cfac|b|) * (sgn(a)/2 + sgn(b)/2), sgn(0) = +1;
+// compression factor 2.0 for the density, 1.5 for the other variables.
+template <typename T>
+__device__ __forceinline__ T mc_slope(T a, T b, T cfac) {
+  T m = fmin(T(0.5) * fabs(a + b), fmin(cfac * fabs(a), cfac * fabs(b)));
+  T sa = a >= T(0) ? T(0.5) : T(-0.5), sb = b >= T(0) ? T(0.5) : T(-0.5);
+  return m * (sa + sb);
+}
+
 template <int N, typename T>
 __device__ __forceinline__ void weno_candidates(const T* d, T c[N + 1][N]) {
   if constexpr (N == 2) weno_candidates_n2<T>(d, c);
@@ -307,15 +319,15 @@ template <typename T> struct Tabs {
 // Each translation unit that reads the tables holds its own constant copy
 // (no relocatable device code); build_tabs (awe_tables.cu) fills host copies
 // and UPLOAD_LOCAL_TABLES() copies them into the calling unit's symbols.
-void build_tabs(Tabs<double>* td, Tabs<float>* tf);  // [2] each, N = 2, 3
-static __constant__ Tabs<double> c_tab_d[2];
-static __constant__ Tabs<float> c_tab_f[2];
+void build_tabs(Tabs<double>* td, Tabs<float>* tf);  // [3] each, N = 1, 2, 3
+static __constant__ Tabs<double> c_tab_d[3];
+static __constant__ Tabs<float> c_tab_f[3];
 template <typename T> __device__ __forceinline__ const Tabs<T>& tabs(int N);
-template <> __device__ __forceinline__ const Tabs<double>& tabs<double>(int N) { return c_tab_d[N - 2]; }
-template <> __device__ __forceinline__ const Tabs<float>& tabs<float>(int N) { return c_tab_f[N - 2]; }
+template <> __device__ __forceinline__ const Tabs<double>& tabs<double>(int N) { return c_tab_d[N - 1]; }
+template <> __device__ __forceinline__ const Tabs<float>& tabs<float>(int N) { return c_tab_f[N - 1]; }
 static inline cudaError_t upload_local_tables(cudaStream_t s) {
-  Tabs<double> td[2];
-  Tabs<float> tf[2];
+  Tabs<double> td[3];
+  Tabs<float> tf[3];
   build_tabs(td, tf);
   cudaError_t e = cudaMemcpyToSymbolAsync(c_tab_d, td, sizeof(td), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tab_f, tf, sizeof(tf), 0, cudaMemcpyHostToDevice, s);

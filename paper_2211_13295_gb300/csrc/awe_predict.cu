@@ -196,6 +196,53 @@ __device__ __forceinline__ bool state_physical5(const T* u, T gm1) {
   return state_physical<3, T>(u, gm1);
 }
 
+// Stages of the factorised kernel with static lane mappings (each lane owns
+// fixed indices, the rest are compile-time loops with constant-bank basis
+// operands) versus strided item loops over all 32 lanes.  The static forms
+// leave some lanes idle in a few stages; that pays in FP32, where the
+// kernel is issue-bound, but not in FP64, where the DP pipe is charged
+// per warp instruction whatever the active lane count.
+enum : unsigned { kStT2 = 1, kStE1 = 2, kStE2 = 4, kStE3 = 8, kStP1 = 16, kStP2 = 32 };
+template <typename T> constexpr unsigned kStatic = sizeof(T) == 4 ? 0x3Fu : 0u;
+
+// compile-time positions in the enumerations used by the factorised kernel
+__host__ __device__ constexpr int p3idx(int b, int c) { return c * 4 - c * (c - 1) / 2 + b; }   // b+c <= 3, c outer
+__host__ __device__ constexpr int p2idx(int p, int e) { return e * 3 - e * (e - 1) / 2 + p; }   // p+e <= 2, e outer
+__host__ __device__ constexpr int simplex_idx(int M, int a, int b, int c) {                     // a+b+c <= M, c outer
+  int idx = 0;
+  for (int cc = 0; cc < c; ++cc) idx += (M - cc + 1) * (M - cc + 2) / 2;
+  for (int bb = 0; bb < b; ++bb) idx += M - c - bb + 1;
+  return idx + a;
+}
+__host__ __device__ constexpr int tri2idx(int p, int q, int r) { return simplex_idx(2, p, q, r); }
+__host__ __device__ constexpr int gmidx(int a, int b, int c, int e) {                            // G-modes, e outer
+  return (e == 0 ? 0 : e == 1 ? 10 : 14) + simplex_idx(2 - e, a, b, c);
+}
+// the (p, q, r) of tri2 index t, as compile-time functions
+__host__ __device__ constexpr int tri2_p(int t) {
+  for (int r = 0; r <= 2; ++r)
+    for (int q = 0; q <= 2 - r; ++q)
+      for (int p = 0; p <= 2 - r - q; ++p)
+        if (tri2idx(p, q, r) == t) return p;
+  return -1;
+}
+__host__ __device__ constexpr int tri2_q(int t) {
+  for (int r = 0; r <= 2; ++r)
+    for (int q = 0; q <= 2 - r; ++q)
+      for (int p = 0; p <= 2 - r - q; ++p)
+        if (tri2idx(p, q, r) == t) return q;
+  return -1;
+}
+__host__ __device__ constexpr int tri2_r(int t) {
+  for (int r = 0; r <= 2; ++r)
+    for (int q = 0; q <= 2 - r; ++q)
+      for (int p = 0; p <= 2 - r - q; ++p)
+        if (tri2idx(p, q, r) == t) return r;
+  return -1;
+}
+__host__ __device__ constexpr int pair2_p(int pe) { return pe < 3 ? pe : pe < 5 ? pe - 3 : 0; }
+__host__ __device__ constexpr int pair2_e(int pe) { return pe < 3 ? 0 : pe < 5 ? 1 : 2; }
+
 template <typename T, int EMAX>
 __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const FactIdx& ix, int lane,
                                              const T lam[3]) {
@@ -206,45 +253,91 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   T* Y2 = z + FactSmem<T>::R1;               // [v][n2][pe]    one direction (pe stride 6)
   T* Y3 = z + FactSmem<T>::R1 + 480;         // [d][v][n1][tri] (tri stride 10)
   // one direction at a time: P1 contracts the first dimension (z for d = x,
-  // y; y for d = z), P2 the second (y for d = x; x for d = y, z)
+  // y; y for d = z), P2 the second (y for d = x; x for d = y, z).  Static lane
+  // mappings (kStatic): P1 lanes own (n2, half of the (p,e) pairs), P2 lanes
+  // own (n1, v); the remaining indices are compile-time loops, so the basis
+  // values are uniform constant-bank operands.
+  const Tabs<T>& tc = tabs<T>(3);
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-#pragma unroll 2
-    for (int it = lane; it < 5 * 16 * NPE; it += 32) {
-      int pe = it % NPE;
-      int rest = it / NPE;
-      int n2 = rest % 16;
-      int v = rest / 16;
-      int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
-      int a0 = n2 & 3, a1 = n2 >> 2;
-      T acc = T(0);
+    if constexpr ((kStatic<T> & kStP1) != 0) {
+      {
+        const int n2 = lane & 15, h = lane >> 4;
+        const int a0 = n2 & 3, a1 = n2 >> 2;
+        const int sbase = d < 2 ? (a0 + 4 * a1) : (a0 + 16 * a1);
+        const int sstr = d < 2 ? 16 : 4;
+        const T* y1 = Y1 + (d * 5) * 64 * 3;
+        // the (p,e) pairs of this half of the warp
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        // d < 2: n2 = (i,j), sum over k; d = 2: n2 = (i,k), sum over j
-        int s = d < 2 ? (a0 + 4 * a1 + 16 * m) : (a0 + 4 * m + 16 * a1);
-        acc = fma(Y1[((d * 5 + v) * 64 + s) * 3 + e], tb.WPN[p][m], acc);
+        for (int pe = 0; pe < NPE; ++pe) {
+          if ((pe & 1) != h) continue;
+          const int p = pair2_p(pe), e = pair2_e(pe);
+#pragma unroll 1
+          for (int v = 0; v < 5; ++v) {
+            const T* yv = y1 + v * 64 * 3 + sbase * 3 + e;
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc = fma(yv[m * sstr * 3], tc.WPN[p][m], acc);
+            Y2[(v * 16 + n2) * 6 + pe] = acc;
+          }
+        }
       }
-      Y2[(v * 16 + n2) * 6 + pe] = acc;
+    } else {
+#pragma unroll 2
+      for (int it = lane; it < 5 * 16 * NPE; it += 32) {
+        int pe = it % NPE;
+        int rest = it / NPE;
+        int n2 = rest % 16;
+        int v = rest / 16;
+        int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
+        int a0 = n2 & 3, a1 = n2 >> 2;
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          // d < 2: n2 = (i,j), sum over k; d = 2: n2 = (i,k), sum over j
+          int s = d < 2 ? (a0 + 4 * a1 + 16 * m) : (a0 + 4 * m + 16 * a1);
+          acc = fma(Y1[((d * 5 + v) * 64 + s) * 3 + e], tb.WPN[p][m], acc);
+        }
+        Y2[(v * 16 + n2) * 6 + pe] = acc;
+      }
     }
     __syncwarp();
-#pragma unroll 2
-    for (int it = lane; it < 5 * 4 * NTR; it += 32) {
-      int tr = it % NTR;
-      int rest = it / NTR;
-      int n1 = rest % 4;
-      int v = rest / 4;
-      int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
-      // d = x: Y3[i][(b,c,e)] = sum_j Y2[(i,j)][(c,e)] WPN[b][j]      (p=b, qq=c)
-      // d = y: Y3[j][(a,c,e)] = sum_i Y2[(i,j)][(c,e)] WPN[a][i]      (p=a, qq=c)
-      // d = z: Y3[k][(a,b,e)] = sum_i Y2[(i,k)][(b,e)] WPN[a][i]      (p=a, qq=b)
-      int pe = ix.pair2_idx[qq][e];
-      T acc = T(0);
+    if constexpr ((kStatic<T> & kStP2) != 0) {
+      if (lane < 20) {
+        const int n1 = lane & 3, v = lane >> 2;
+        const int nbase = d == 0 ? n1 : 4 * n1;
+        const int nstr = d == 0 ? 4 : 1;
+        const T* y2 = Y2 + v * 16 * 6;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int n2 = d == 0 ? (n1 + 4 * m) : (m + 4 * n1);
-        acc = fma(Y2[(v * 16 + n2) * 6 + pe], tb.WPN[p][m], acc);
+        for (int tr = 0; tr < NTR; ++tr) {
+          const int p = tri2_p(tr), qq = tri2_q(tr), e = tri2_r(tr);
+          const int pe = p2idx(qq, e);
+          T acc = T(0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) acc = fma(y2[(nbase + m * nstr) * 6 + pe], tc.WPN[p][m], acc);
+          Y3[((d * 5 + v) * 4 + n1) * 10 + tr] = acc;
+        }
       }
-      Y3[((d * 5 + v) * 4 + n1) * 10 + tr] = acc;
+    } else {
+#pragma unroll 2
+      for (int it = lane; it < 5 * 4 * NTR; it += 32) {
+        int tr = it % NTR;
+        int rest = it / NTR;
+        int n1 = rest % 4;
+        int v = rest / 4;
+        int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
+        // d = x: Y3[i][(b,c,e)] = sum_j Y2[(i,j)][(c,e)] WPN[b][j]      (p=b, qq=c)
+        // d = y: Y3[j][(a,c,e)] = sum_i Y2[(i,j)][(c,e)] WPN[a][i]      (p=a, qq=c)
+        // d = z: Y3[k][(a,b,e)] = sum_i Y2[(i,k)][(b,e)] WPN[a][i]      (p=a, qq=b)
+        int pe = ix.pair2_idx[qq][e];
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int n2 = d == 0 ? (n1 + 4 * m) : (m + 4 * n1);
+          acc = fma(Y2[(v * 16 + n2) * 6 + pe], tb.WPN[p][m], acc);
+        }
+        Y3[((d * 5 + v) * 4 + n1) * 10 + tr] = acc;
+      }
     }
     __syncwarp();
   }
@@ -318,22 +411,62 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
         T1[it] = acc;
       }
       __syncwarp();
-#pragma unroll 2
-      for (int it = lane; it < 320; it += 32) {
-        int c = it % 4, rest = it / 4, j = rest % 4, rest2 = rest / 4, i = rest2 % 4, v = rest2 / 4;
-        T acc = T(0);
-        for (int b = 0; b <= 3 - c; ++b) acc = fma(T1[(v * 4 + i) * 10 + ix.pair3_idx[b][c]], tb.PN[b][j], acc);
-        T2[it] = acc;
-      }
-      __syncwarp();
-#pragma unroll 2
-      for (int it = lane; it < 320; it += 32) {
-        int s = it % 64, v = it / 64;
-        int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
-        T acc = T(0);
+      if constexpr ((kStatic<T> & kStT2) != 0) {
+        {
+          // T2[v][i][j][c]: lanes own (i, j) and half of the variables
+          const int i = lane & 3, j = (lane >> 2) & 3, h = lane >> 4;
+          T pnj[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc = fma(T2[((v * 4 + i) * 4 + j) * 4 + c], tb.PN[c][k], acc);
-        swn[v * 64 + s] = acc;
+          for (int b = 0; b < 4; ++b) pnj[b] = tb.PN[b][j];
+#pragma unroll 1
+          for (int v = h; v < 5; v += 2) {
+            const T* t1 = T1 + (v * 4 + i) * 10;
+            T* t2 = T2 + ((v * 4 + i) * 4 + j) * 4;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              T acc = T(0);
+#pragma unroll
+              for (int b = 0; b <= 3 - c; ++b) acc = fma(t1[p3idx(b, c)], pnj[b], acc);
+              t2[c] = acc;
+            }
+          }
+        }
+        __syncwarp();
+        // w at the spatial nodes: lanes own the nodes s = lane and lane + 32
+#pragma unroll
+        for (int hs = 0; hs < 2; ++hs) {
+          const int s = lane + 32 * hs;
+          const int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
+          T pnk[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) pnk[c] = tb.PN[c][k];
+#pragma unroll 1
+          for (int v = 0; v < 5; ++v) {
+            const T* t2 = T2 + ((v * 4 + i) * 4 + j) * 4;
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc = fma(t2[c], pnk[c], acc);
+            swn[v * 64 + s] = acc;
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int it = lane; it < 320; it += 32) {
+          int c = it % 4, rest = it / 4, j = rest % 4, rest2 = rest / 4, i = rest2 % 4, v = rest2 / 4;
+          T acc = T(0);
+          for (int b = 0; b <= 3 - c; ++b) acc = fma(T1[(v * 4 + i) * 10 + ix.pair3_idx[b][c]], tb.PN[b][j], acc);
+          T2[it] = acc;
+        }
+        __syncwarp();
+#pragma unroll 2
+        for (int it = lane; it < 320; it += 32) {
+          int s = it % 64, v = it / 64;
+          int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
+          T acc = T(0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc = fma(T2[((v * 4 + i) * 4 + j) * 4 + c], tb.PN[c][k], acc);
+          swn[v * 64 + s] = acc;
+        }
       }
       __syncwarp();
     }
@@ -359,34 +492,94 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
       T* A = z + FactSmem<T>::R2;   // [v][tri][t]        200 (dead before Y1 is written)
       T* B = A + 200;               // [v][i][pair2][t]   480 (dead before Y1 is written)
       T* C = z + FactSmem<T>::R1;   // [v][i][j][c][t]    960
-      // E1: A[v][(a,b,c)][t] = sum_e g[(a,b,c,e)] I_e(tau_t)
+      // E1: A[v][(a,b,c)][t] = sum_e g[(a,b,c,e)] I_e(tau_t); lanes own (t, v)
+      if constexpr ((kStatic<T> & kStE1) != 0) {
+        if (lane < 20) {
+          const int t = lane & 3, v = lane >> 2;
+          T it_[3];
+#pragma unroll
+          for (int e = 0; e < 3; ++e) it_[e] = tb.IT[e][t];
+#pragma unroll
+          for (int tr = 0; tr < 10; ++tr) {
+            const int a = tri2_p(tr), b = tri2_q(tr), c = tri2_r(tr);
+            T acc = T(0);
+#pragma unroll
+            for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + gmidx(a, b, c, e)], it_[e], acc);
+            A[(v * 10 + tr) * 4 + t] = acc;
+          }
+        }
+      } else {
 #pragma unroll 2
-      for (int it = lane; it < 200; it += 32) {
-        int t = it % 4, rest = it / 4, tr = rest % 10, v = rest / 10;
-        int a = ix.tri2[tr][0], b = ix.tri2[tr][1], c = ix.tri2[tr][2];
-        T acc = T(0);
-        for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + ix.gidx[a][b][c][e]], tb.IT[e][t], acc);
-        A[it] = acc;
+        for (int it = lane; it < 200; it += 32) {
+          int t = it % 4, rest = it / 4, tr = rest % 10, v = rest / 10;
+          int a = ix.tri2[tr][0], b = ix.tri2[tr][1], c = ix.tri2[tr][2];
+          T acc = T(0);
+          for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + ix.gidx[a][b][c][e]], tb.IT[e][t], acc);
+          A[it] = acc;
+        }
       }
       __syncwarp();
-      // E2: B[v][i][(b,c)][t] = sum_a A[(a,b,c)][t] P_a(x_i)
+      // E2: B[v][i][(b,c)][t] = sum_a A[(a,b,c)][t] P_a(x_i); lanes own (i, t, half of v)
+      if constexpr ((kStatic<T> & kStE2) != 0) {
+        {
+          const int i = lane & 3, t = (lane >> 2) & 3, h = lane >> 4;
+          T pni[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) pni[a] = tb.PN[a][i];
+#pragma unroll 1
+          for (int v = h; v < 5; v += 2) {
+#pragma unroll
+            for (int pc = 0; pc < 6; ++pc) {
+              const int b = pair2_p(pc), c = pair2_e(pc);
+              T acc = T(0);
+#pragma unroll
+              for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + tri2idx(a, b, c)) * 4 + t], pni[a], acc);
+              B[((v * 4 + i) * 6 + pc) * 4 + t] = acc;
+            }
+          }
+        }
+      } else {
 #pragma unroll 2
-      for (int it = lane; it < 480; it += 32) {
-        int t = it % 4, rest = it / 4, pc = rest % 6, rest2 = rest / 6, i = rest2 % 4, v = rest2 / 4;
-        int b = ix.pair2[pc][0], c = ix.pair2[pc][1];
-        T acc = T(0);
-        for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + ix.tri_idx[a][b][c]) * 4 + t], tb.PN[a][i], acc);
-        B[it] = acc;
+        for (int it = lane; it < 480; it += 32) {
+          int t = it % 4, rest = it / 4, pc = rest % 6, rest2 = rest / 6, i = rest2 % 4, v = rest2 / 4;
+          int b = ix.pair2[pc][0], c = ix.pair2[pc][1];
+          T acc = T(0);
+          for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + ix.tri_idx[a][b][c]) * 4 + t], tb.PN[a][i], acc);
+          B[it] = acc;
+        }
       }
       __syncwarp();
-      // E3: C[v][i][j][c][t] = sum_b B[i][(b,c)][t] P_b(y_j)
+      // E3: C[v][i][j][c][t] = sum_b B[i][(b,c)][t] P_b(y_j); lanes own (i, j, parity of t)
+      if constexpr ((kStatic<T> & kStE3) != 0) {
+        {
+          const int i = lane & 3, j = (lane >> 2) & 3, h = lane >> 4;
+          T pnj[3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) pnj[b] = tb.PN[b][j];
+#pragma unroll 1
+          for (int v = 0; v < 5; ++v) {
+#pragma unroll
+            for (int tt = 0; tt < 2; ++tt) {
+              const int t = h + 2 * tt;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                T acc = T(0);
+#pragma unroll
+                for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + p2idx(b, c)) * 4 + t], pnj[b], acc);
+                C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t] = acc;
+              }
+            }
+          }
+        }
+      } else {
 #pragma unroll 2
-      for (int it = lane; it < 960; it += 32) {
-        int t = it % 4, rest = it / 4, c = rest % 3, rest2 = rest / 3, j = rest2 % 4, rest3 = rest2 / 4;
-        int i = rest3 % 4, v = rest3 / 4;
-        T acc = T(0);
-        for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + ix.pair2_idx[b][c]) * 4 + t], tb.PN[b][j], acc);
-        C[it] = acc;
+        for (int it = lane; it < 960; it += 32) {
+          int t = it % 4, rest = it / 4, c = rest % 3, rest2 = rest / 3, j = rest2 % 4, rest3 = rest2 / 4;
+          int i = rest3 % 4, v = rest3 / 4;
+          T acc = T(0);
+          for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + ix.pair2_idx[b][c]) * 4 + t], tb.PN[b][j], acc);
+          C[it] = acc;
+        }
       }
       __syncwarp();
       // nodes: q = wn - sum_c C P_c(z_k); fluxes; time contraction into Y1
@@ -394,6 +587,9 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
       const Tabs<T>& tc = tabs<T>(3);
       for (int s = lane; s < 64; s += 32) {
         int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
+        T pnk[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pnk[c] = tb.PN[c][k];
         T acc[3][5][3];
 #pragma unroll
         for (int d = 0; d < 3; ++d)
@@ -408,7 +604,7 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
           for (int v = 0; v < 5; ++v) {
             T x = swn[v * 64 + s];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], tb.PN[c][k], x);
+            for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
             qn[v] = x;
           }
           phys_fluxes<3, T>(qn, gm1, F);
@@ -635,8 +831,10 @@ void launch_predict_tab(const Geo& q, int prec, int picard, const void* W, const
                                                                  (float*)FS);                    \
     return;                                                                                      \
   }
+  AWE_PD(2, 1)
   AWE_PD(2, 2)
   AWE_PD(2, 3)
+  AWE_PD(3, 1)
   AWE_PD(3, 2)
 #undef AWE_PD
 }

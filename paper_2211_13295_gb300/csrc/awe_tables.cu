@@ -56,7 +56,10 @@ static double derivD(int ap, int a) {  // coefficient of P_a in dP_ap/dx
 }
 
 void gauss_nodes(int n, double* x, double* w) {
-  if (n == 2) {
+  if (n == 1) {
+    x[0] = 0.0;
+    w[0] = 1.0;
+  } else if (n == 2) {
     double a = 0.5 / std::sqrt(3.0);
     x[0] = -a; x[1] = a;
     w[0] = w[1] = 0.5;
@@ -118,8 +121,8 @@ template <typename A, typename B> static void cast_tabs(const Tabs<A>& s, Tabs<B
 }
 
 void build_tabs(Tabs<double>* td, Tabs<float>* tf) {
-  for (int k = 0; k < 2; ++k) {
-    make_tabs(k + 2, td[k]);
+  for (int k = 0; k < 3; ++k) {
+    make_tabs(k + 1, td[k]);
     cast_tabs(td[k], tf[k]);
   }
 }
@@ -157,7 +160,8 @@ PTabLayout ptab_layout(int D, int N) {
   L.nnodes = L.nsn * nn;
   L.ns = (int)spatial_modes(D, N).size();
   L.ng = (int)st_modes(D, N - 1).size();
-  L.nfq = D == 2 ? 4 : 8;
+  const int nq = (N + 2) / 2;
+  L.nfq = D == 2 ? nq * nq : nq * nq * nq;
   size_t off = 0;
   L.ev = off; off += (size_t)L.nnodes * L.ng;
   L.kp = off; off += (size_t)D * L.nnodes * L.ng;
@@ -173,9 +177,10 @@ std::vector<double> ptab_build(int D, int N) {
   PTabLayout L = ptab_layout(D, N);
   std::vector<double> t(L.total, 0.0);
   const int nn = N + 1;
+  const int nq = (N + 2) / 2;
   double x[4], w[4], xf[2], wf[2];
   gauss_nodes(nn, x, w);
-  gauss_nodes(2, xf, wf);
+  gauss_nodes(nq, xf, wf);
   auto sm = spatial_modes(D, N);
   auto gm = st_modes(D, N - 1);
   auto node_xyz = [&](int s, int* ix) {
@@ -234,7 +239,7 @@ std::vector<double> ptab_build(int D, int N) {
       }
     for (int side = 0; side < 2; ++side)
       for (int q = 0; q < L.nfq; ++q) {
-        int i1 = q % 2, i2 = D == 3 ? (q / 2) % 2 : 0, it = D == 3 ? q / 4 : q / 2;
+        int i1 = q % nq, i2 = D == 3 ? (q / nq) % nq : 0, it = D == 3 ? q / (nq * nq) : q / nq;
         double xi[3] = {0, 0, 0};
         xi[d] = side ? 0.5 : -0.5;
         xi[t1] = xf[i1];

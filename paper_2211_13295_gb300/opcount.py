@@ -115,7 +115,8 @@ def predictor_flops(D, N, picard):
     NG0 = comb(N - 1 + D, D)
     NN = N + 1
     NSN = NN ** D
-    NFQ = 4 if D == 2 else 8
+    nq = (N + 2) // 2
+    NFQ = nq ** D
     flops = divs = 0
     if picard >= 1:
         flops += NSN * (2 * nv * NS + fn + D * nv * (1 + 2 * NG0))
@@ -128,9 +129,10 @@ def predictor_flops(D, N, picard):
     return flops, divs
 
 
-def flux_flops(D):
-    """flops and divs+sqrt per face of the flux kernel (2 or 4 transverse x 2 time points)."""
-    nfq = 4 if D == 2 else 8
+def flux_flops(D, N=2):
+    """flops and divs+sqrt per face of the flux kernel (Gauss points per face:
+    1 at order 2, 2 per transverse dimension and in time at orders 3 and 4)."""
+    nfq = ((N + 2) // 2) ** D
     h, hd = _hllc(D)
     return nfq * (h + 2 * (D + 2)), nfq * hd
 
@@ -158,7 +160,7 @@ def step_flops_per_zone(prob, picard=None, gate_linear_fraction=0.0):
     }
     pf, pd = predictor_flops(D, N, picard)
     out["predictor"] = (pf * box / nact, pd * box / nact)
-    ff, fd = flux_flops(D)
+    ff, fd = flux_flops(D, N)
     nfaces = sum((n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)) for d in range(D))
     out["hllc_flux"] = (ff * nfaces / nact, fd * nfaces / nact)
     uf, ud = update_flops(D)

@@ -163,24 +163,59 @@ def jump_gate(nin, N, thresh=0.5):
     return p
 
 
+def run_one_status(awe, prob, U0, gate=None, slab=0):
+    """run_one that tolerates the non-physical status: returns (U1, dt, code)"""
+    g = awe.Grid(prob, gate=gate is not None, slab=slab)
+    if gate is not None:
+        g.gate_set_weights(gate)
+    g.set_state(U0)
+    dt = g.cfl_dt()
+    g.step(dt, sync=False)
+    code = 0
+    try:
+        g.check()
+    except awe.AweError as e:
+        code = e.code
+    U1 = g.get_state()
+    g.close()
+    return U1, dt, code
+
+
+def nonphysical_zones(U, gamma):
+    rho = U[0]
+    with np.errstate(all="ignore"):
+        p = (gamma - 1.0) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / rho)
+        return np.argwhere(~((rho > 0) & (p > 0) & np.isfinite(p)))
+
+
 def test_blast_384_order4_gate_fallback_slabbed(awe):
     """Blast on 384^3, order 4, FP64 with the positivity fallback,
-    slab-streamed (128 planes): windows on the sphere's surface against the
-    oracle, first with full WENO, then with a gate that flags large stencil
-    jumps (the oracle computes its own flags)."""
+    slab-streamed (128 planes), first with full WENO, then with a gate that
+    flags large stencil jumps (the oracle computes its own flags).
+
+    At this size the first step leaves a few zones just outside the sphere's
+    surface with negative pressure, in the oracle as on the GPU: the fallback
+    keeps the face states and hence the Riemann problems physical, not the
+    updated means.  The test therefore checks (a) that the GPU reports the
+    non-physical status exactly when its state holds such zones, (b) windows
+    around those zones against the oracle (same values, so the oracle finds
+    the same zones non-physical), and (c) windows on the sphere's surface."""
     prob = P.blast3d(n=384, order=4).replace(fallback=True)
     nin, _ = awe.gate_dims(3, 4)
     U0 = prob.initial_state()
     n = 384
     r0 = int(0.5 * n + 0.2 * n) - 2
-    centers = [[r0, n // 2, n // 2], [n // 2, r0, n // 2 - 3], [n // 2 - 2, n // 2, r0], [100, 120, 140]]
-    U1, dt = run_one(awe, prob, U0, slab=128)
-    errs = sampled_windows(prob, U0, U1, dt, 0.0, nwin=4, m=4, seed=3, centers=centers)
-    assert max(errs) <= 1e-12, errs
+    surface = [[r0, n // 2, n // 2], [n // 2, r0, n // 2 - 3], [n // 2 - 2, n // 2, r0], [100, 120, 140]]
     params = jump_gate(nin, 3)
-    U1g, dtg = run_one(awe, prob, U0, gate=params, slab=128)
-    errs = sampled_windows(prob, U0, U1g, dtg, 0.0, nwin=4, m=4, seed=3, flags_params=params, centers=centers)
-    assert max(errs) <= 1e-12, errs
+    for gate in (None, params):
+        U1, dt, code = run_one_status(awe, prob, U0, gate=gate, slab=128)
+        bad = nonphysical_zones(U1, prob.gamma)
+        assert code == (awe.AWE_ERR_NONPHYSICAL if len(bad) else awe.AWE_OK), (code, len(bad))
+        centers = [[min(max(int(i) - 1, 0), n - 4), min(max(int(j) - 1, 0), n - 4), min(max(int(k) - 1, 0), n - 4)]
+                   for (k, j, i) in bad[:3]] + surface
+        errs = sampled_windows(prob, U0, U1, dt, 0.0, nwin=len(centers), m=4, seed=3,
+                               flags_params=gate, centers=centers)
+        assert max(errs) <= 1e-12, (gate is not None, errs)
 
 
 def test_kh_512_order4_fp32_gate_slabbed(awe):
