@@ -67,11 +67,26 @@ typedef enum {
                          CFL reduction in FP64 */
 } awe_prec;
 
+/* Riemann solvers of the corrector (Sec. I.1 names HLLC, HLL, HLLEM and
+ * Rusanov).  All use the same face and time quadrature.  HLL, HLLC and HLLEM
+ * take Davis-Einfeldt wave speeds from Roe averages; HLLEM restores the
+ * contact and shear waves of HLL with the anti-diffusion coefficient
+ * 1 - min(u~,0)/S_L - max(u~,0)/S_R; Rusanov's speed is
+ * max(|u_L| + c_L, |u_R| + c_R). */
+typedef enum {
+  AWE_RS_HLLC = 0,
+  AWE_RS_HLL = 1,
+  AWE_RS_HLLEM = 2,
+  AWE_RS_RUSANOV = 3
+} awe_riemann;
+
 typedef struct {
   int dim;               /* 2 or 3 */
   int n[3];              /* active zones per dimension (n[2] ignored in 2D) */
   double lo[3], hi[3];   /* domain box (lo[2], hi[2] ignored in 2D) */
-  int order;             /* 3 or 4 (polynomial degree N = order - 1) */
+  int order;             /* 2, 3 or 4 (polynomial degree N = order - 1; order 2
+                            is the paper's own scheme: MC-limited slopes of
+                            Fig. 3, one predictor sweep, one face point) */
   double gamma;          /* ratio of specific heats, ideal gas */
   int bc[6];             /* awe_bc per face */
   double inflow[6][5];   /* conserved state per face (AWE_BC_INFLOW / DMR post-shock) */
@@ -89,6 +104,7 @@ typedef struct {
                             whose face states have rho <= 0, p <= 0 or a
                             non-finite value uses its zone mean as every face
                             state (first order) */
+  int riemann;           /* awe_riemann: the corrector's Riemann solver */
 } awe_config;
 
 /* Create a grid (allocates all device memory).  Cites: Fig. 1 data region.

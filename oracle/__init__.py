@@ -29,6 +29,7 @@ class OraCfg(C.Structure):
         ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("gamma", C.c_double),
         ("eps", C.c_double), ("lin", C.c_double * 4), ("bc", C.c_int * 6),
         ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5), ("fallback", C.c_int),
+        ("riemann", C.c_int),
     ]
 
 
@@ -51,6 +52,7 @@ def lib():
             "ora_beta": (C.c_double, [C.c_int, dp]),
             "ora_weno1d": (None, [C.c_int, dp, C.c_double, dp, C.c_int, dp, dp]),
             "ora_hllc": (None, [C.c_int, C.c_double, C.c_int, dp, dp, dp]),
+            "ora_riemann": (None, [C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, dp]),
             "ora_mc_slope": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "ora_phys_flux": (None, [C.c_int, C.c_double, C.c_int, dp, dp]),
             "ora_ghosted_size": (C.c_size_t, [cp]),
@@ -149,6 +151,19 @@ def hllc(dim, gamma, direction, UL, UR):
     return F
 
 
+RIEMANN = {"hllc": 0, "hll": 1, "hllem": 2, "rusanov": 3}
+
+
+def riemann(kind, dim, gamma, direction, UL, UR):
+    """Numerical flux of one of the Riemann solvers ("hllc", "hll", "hllem",
+    "rusanov")."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    UR = np.ascontiguousarray(UR, dtype=np.float64)
+    F = np.zeros(dim + 2)
+    lib().ora_riemann(RIEMANN[kind], dim, gamma, direction, _dp(UL), _dp(UR), _dp(F))
+    return F
+
+
 def phys_flux(dim, gamma, direction, U):
     U = np.ascontiguousarray(U, dtype=np.float64)
     F = np.zeros(dim + 2)
@@ -194,6 +209,7 @@ class Oracle:
             for v in range(len(prob.pre)):
                 c.pre[v] = prob.pre[v]
         c.fallback = 1 if getattr(prob, "fallback", False) else 0
+        c.riemann = RIEMANN[getattr(prob, "riemann", "hllc")]
         self.cfg = c
         self.dim = prob.dim
         self.nv = prob.dim + 2

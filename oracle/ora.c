@@ -562,6 +562,131 @@ void ora_hllc(int dim, double gamma, int dir, const double* UL, const double* UR
   }
 }
 
+/* The other Riemann solvers the paper names beside HLLC (Sec. I.1): HLL,
+ * HLLEM and Rusanov.  Readings (the paper gives no formulas):
+ *  - HLL (Harten, Lax and van Leer): the single intermediate state between the
+ *    Davis-Einfeldt speeds S_L, S_R of ora_hllc; F = F_L if 0 <= S_L, F_R if
+ *    S_R <= 0, else (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+ *  - HLLEM (Einfeldt; in the anti-diffusive form of Dumbser and Balsara):
+ *    HLL with the linearly degenerate waves (the contact and the dim-1 shear
+ *    waves, all moving with the Roe velocity u~) restored.  Their Roe
+ *    strengths are a_c = drho - dp/c~^2 along r_c = (1, v~, |v~|^2/2) and
+ *    a_t = rho~ dv_t along r_t = (0, e_t, v~_t); inside the fan the HLL jump
+ *    term S_L S_R dU becomes S_L S_R (dU - delta sum_k a_k r_k) with
+ *    delta = 1 - min(u~,0)/S_L - max(u~,0)/S_R, which makes isolated
+ *    contacts and shear waves exact for any speeds bracketing u~.
+ *  - Rusanov (local Lax-Friedrichs): F = (F_L + F_R)/2 - S (U_R - U_L)/2 with
+ *    S = max(|u_L| + c_L, |u_R| + c_R), the normal velocity u. */
+typedef struct {
+  double rl, rr, vl[3], vr[3], pl, pr, cl, cr, El, Er;
+  double rt, vt[3], vt2, ct, SL, SR;
+} ora_rs_states;
+
+static void rs_states(int dim, double gamma, int dir, const double* UL, const double* UR,
+                      ora_rs_states* w) {
+  const int nv = dim + 2;
+  w->rl = UL[0];
+  w->rr = UR[0];
+  double kl = 0.0, kr = 0.0;
+  for (int d = 0; d < 3; ++d) w->vl[d] = w->vr[d] = w->vt[d] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    w->vl[d] = UL[1 + d] / w->rl;
+    w->vr[d] = UR[1 + d] / w->rr;
+    kl += 0.5 * w->rl * w->vl[d] * w->vl[d];
+    kr += 0.5 * w->rr * w->vr[d] * w->vr[d];
+  }
+  w->El = UL[nv - 1];
+  w->Er = UR[nv - 1];
+  w->pl = (gamma - 1.0) * (w->El - kl);
+  w->pr = (gamma - 1.0) * (w->Er - kr);
+  w->cl = sqrt(gamma * w->pl / w->rl);
+  w->cr = sqrt(gamma * w->pr / w->rr);
+  double sl = sqrt(w->rl), sr = sqrt(w->rr);
+  w->rt = sl * sr;
+  w->vt2 = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    w->vt[d] = (sl * w->vl[d] + sr * w->vr[d]) / (sl + sr);
+    w->vt2 += w->vt[d] * w->vt[d];
+  }
+  double Hl = (w->El + w->pl) / w->rl, Hr = (w->Er + w->pr) / w->rr;
+  double Ht = (sl * Hl + sr * Hr) / (sl + sr);
+  w->ct = sqrt((gamma - 1.0) * (Ht - 0.5 * w->vt2));
+  w->SL = fmin(w->vl[dir] - w->cl, w->vt[dir] - w->ct);
+  w->SR = fmax(w->vr[dir] + w->cr, w->vt[dir] + w->ct);
+}
+
+/* HLL and HLLEM share everything but the restored waves (hllem = 0 or 1). */
+static void hll_family(int dim, double gamma, int dir, const double* UL, const double* UR,
+                       int hllem, double* F) {
+  const int nv = dim + 2;
+  ora_rs_states w;
+  rs_states(dim, gamma, dir, UL, UR, &w);
+  double FL[MAXV], FR[MAXV];
+  ora_phys_flux(dim, gamma, dir, UL, FL);
+  ora_phys_flux(dim, gamma, dir, UR, FR);
+  if (0.0 <= w.SL) {
+    for (int s = 0; s < nv; ++s) F[s] = FL[s];
+    return;
+  }
+  if (w.SR <= 0.0) {
+    for (int s = 0; s < nv; ++s) F[s] = FR[s];
+    return;
+  }
+  double jump[MAXV];
+  for (int s = 0; s < nv; ++s) jump[s] = UR[s] - UL[s];
+  if (hllem) {
+    double ut = w.vt[dir];
+    double delta = 1.0 - fmin(ut, 0.0) / w.SL - fmax(ut, 0.0) / w.SR;
+    double ac = (w.rr - w.rl) - (w.pr - w.pl) / (w.ct * w.ct);
+    double rwave[MAXV];
+    /* contact */
+    rwave[0] = 1.0;
+    for (int d = 0; d < dim; ++d) rwave[1 + d] = w.vt[d];
+    rwave[nv - 1] = 0.5 * w.vt2;
+    for (int s = 0; s < nv; ++s) jump[s] -= delta * ac * rwave[s];
+    /* shear waves */
+    for (int t = 0; t < dim; ++t) {
+      if (t == dir) continue;
+      double at = w.rt * (w.vr[t] - w.vl[t]);
+      for (int s = 0; s < nv; ++s) rwave[s] = 0.0;
+      rwave[1 + t] = 1.0;
+      rwave[nv - 1] = w.vt[t];
+      for (int s = 0; s < nv; ++s) jump[s] -= delta * at * rwave[s];
+    }
+  }
+  for (int s = 0; s < nv; ++s)
+    F[s] = (w.SR * FL[s] - w.SL * FR[s] + w.SL * w.SR * jump[s]) / (w.SR - w.SL);
+}
+
+void ora_hll(int dim, double gamma, int dir, const double* UL, const double* UR, double* F) {
+  hll_family(dim, gamma, dir, UL, UR, 0, F);
+}
+
+void ora_hllem(int dim, double gamma, int dir, const double* UL, const double* UR, double* F) {
+  hll_family(dim, gamma, dir, UL, UR, 1, F);
+}
+
+void ora_rusanov(int dim, double gamma, int dir, const double* UL, const double* UR, double* F) {
+  const int nv = dim + 2;
+  ora_rs_states w;
+  rs_states(dim, gamma, dir, UL, UR, &w);
+  double FL[MAXV], FR[MAXV];
+  ora_phys_flux(dim, gamma, dir, UL, FL);
+  ora_phys_flux(dim, gamma, dir, UR, FR);
+  double S = fmax(fabs(w.vl[dir]) + w.cl, fabs(w.vr[dir]) + w.cr);
+  for (int s = 0; s < nv; ++s) F[s] = 0.5 * (FL[s] + FR[s]) - 0.5 * S * (UR[s] - UL[s]);
+}
+
+void ora_riemann(int kind, int dim, double gamma, int dir, const double* UL, const double* UR,
+                 double* F) {
+  switch (kind) {
+    case ORA_RS_HLL: ora_hll(dim, gamma, dir, UL, UR, F); break;
+    case ORA_RS_HLLEM: ora_hllem(dim, gamma, dir, UL, UR, F); break;
+    case ORA_RS_RUSANOV: ora_rusanov(dim, gamma, dir, UL, UR, F); break;
+    default: ora_hllc(dim, gamma, dir, UL, UR, F); break;
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* ADER predictor                                                            */
 /* ------------------------------------------------------------------------ */
@@ -814,7 +939,7 @@ int ora_fluxes(const ora_cfg* c, const double* Ug, const unsigned char* flags, d
           UL[v] = FS[((((size_t)d * 2 + 1) * nfq + p) * nv + v) * nbox + lz];
           UR[v] = FS[((((size_t)d * 2 + 0) * nfq + p) * nv + v) * nbox + rz];
         }
-        ora_hllc(dim, c->gamma, d, UL, UR, Fp);
+        ora_riemann(c->riemann, dim, c->gamma, d, UL, UR, Fp);
         for (int v = 0; v < nv; ++v) acc[v] += wt * Fp[v];
       }
       for (int v = 0; v < nv; ++v) F[off + (size_t)v * nf + f] = acc[v];

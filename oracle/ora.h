@@ -43,6 +43,7 @@ typedef struct {
   double inflow[6][5];  /* fixed conserved state per face (inflow / DMR post-shock) */
   double pre[5];        /* DMR pre-shock conserved state (top boundary) */
   int fallback;         /* 1: positivity fallback of the face states (see ora.c) */
+  int riemann;          /* ORA_RS_*: Riemann solver of the corrector (HLLC by default) */
 } ora_cfg;
 
 /* ---- small building blocks (exported for the pins) ---- */
@@ -56,7 +57,13 @@ double ora_beta(int N, const double* coef);                     /* smoothness of
 void ora_weno1d(int N, const double* u, double eps, const double* lin,
                 int linear_only, double* coef, double* omega);
 double ora_mc_slope(double a, double b, double cfac);           /* order-2 limiter, Fig. 3 */
+enum { ORA_RS_HLLC = 0, ORA_RS_HLL = 1, ORA_RS_HLLEM = 2, ORA_RS_RUSANOV = 3 };
 void ora_hllc(int dim, double gamma, int dir, const double* UL, const double* UR, double* F);
+void ora_hll(int dim, double gamma, int dir, const double* UL, const double* UR, double* F);
+void ora_hllem(int dim, double gamma, int dir, const double* UL, const double* UR, double* F);
+void ora_rusanov(int dim, double gamma, int dir, const double* UL, const double* UR, double* F);
+void ora_riemann(int kind, int dim, double gamma, int dir, const double* UL, const double* UR,
+                 double* F);
 void ora_phys_flux(int dim, double gamma, int dir, const double* U, double* F);
 
 /* ---- whole-grid operations ---- */

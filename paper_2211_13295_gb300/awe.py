@@ -24,6 +24,7 @@ AWE_OK, AWE_ERR_ARG, AWE_ERR_CUDA, AWE_ERR_OOM, AWE_ERR_NONPHYSICAL, AWE_ERR_TIM
     0, -1, -2, -3, -4, -5, -6
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "inflow": 3, "dmr_bottom": 4, "dmr_top": 5}
 PREC = {"fp64": 0, "fp32": 1}
+RIEMANN = {"hllc": 0, "hll": 1, "hllem": 2, "rusanov": 3}
 
 
 class AweError(RuntimeError):
@@ -39,6 +40,7 @@ class AweConfig(C.Structure):
         ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5), ("prec", C.c_int),
         ("picard", C.c_int), ("weno_eps", C.c_double), ("lin", C.c_double * 4), ("cfl", C.c_double),
         ("gate", C.c_int), ("slab", C.c_int), ("fallback", C.c_int),
+        ("riemann", C.c_int),
     ]
 
 
@@ -159,6 +161,7 @@ def make_config(prob, prec="fp64", gate=False, slab=0, cfl=None, picard=None) ->
     c.gate = 1 if gate else 0
     c.slab = slab
     c.fallback = 1 if getattr(prob, "fallback", False) else 0
+    c.riemann = RIEMANN[getattr(prob, "riemann", "hllc")]
     return c
 
 

@@ -278,6 +278,8 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   if (!(c.gamma > 1.0)) return fail(nullptr, AWE_ERR_ARG, "gamma must exceed 1");
   if (c.picard < 0 || c.picard > 8) return fail(nullptr, AWE_ERR_ARG, "picard out of range");
   if (c.slab < 0) return fail(nullptr, AWE_ERR_ARG, "negative slab");
+  if (c.riemann < AWE_RS_HLLC || c.riemann > AWE_RS_RUSANOV)
+    return fail(nullptr, AWE_ERR_ARG, "riemann must be one of AWE_RS_HLLC, AWE_RS_HLL, AWE_RS_HLLEM, AWE_RS_RUSANOV");
   if (c.dim == 3 && c.n[0] * (long long)c.n[1] * c.n[2] > (1LL << 31))
     return fail(nullptr, AWE_ERR_ARG, "grid too large");
   const char* forced = std::getenv("AWE_FAIL_ALLOC");
@@ -312,6 +314,7 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   }
   for (int v = 0; v < 5; ++v) q.pre[v] = c.pre[v];
   q.fallback = c.fallback ? 1 : 0;
+  q.riemann = c.riemann;
   g->slab = (c.dim == 3 && c.slab > 0 && c.slab < c.n[2]) ? c.slab : q.n[2];
   if (c.dim == 2) g->slab = 1;
   g->bytesT = tsize(c.prec);

@@ -2,8 +2,9 @@
 // Fig. 5) and the conservative FP64 update with the CFL reduction of the
 // updated state (Make_dU_dt and Update_U_Timestep, Figs. 6-7).
 //
-// Face flux: F = sum_q w_q HLLC(U_L(q), U_R(q)) over the tensor Gauss-Legendre
-// points of the face (2 per transverse dimension) and of the time step (2),
+// Face flux: F = sum_q w_q RS(U_L(q), U_R(q)) over the tensor Gauss-Legendre
+// points of the face and of the time step (2 per dimension at orders 3 and 4,
+// 1 at order 2), RS one of HLLC (default), HLL, HLLEM or Rusanov,
 // U_L from the upper-face states of the zone below the face, U_R from the
 // lower-face states of the zone above.  Update: U+ = U - sum_d (dt/dx_d)
 // (F_{d,i+1/2} - F_{d,i-1/2}), in FP64 for every form.
@@ -19,7 +20,7 @@ __host__ __device__ __forceinline__ void face_ext(const Geo& q, int d, int z0, i
   E[2] = (q.dim == 3 ? z1 - z0 : 1) + (d == 2);
 }
 
-template <int D, int N, typename T>
+template <int D, int N, typename T, int K>
 __global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, int z1,
                                               const T* __restrict__ FS, T* __restrict__ F) {
   constexpr int NV = D + 2, NFQ = Modes<D, N>::NFQ;
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, 
         UL[v] = FS[((((long long)d * 2 + 1) * NFQ + p) * NV + v) * nb + lz];
         UR[v] = FS[((((long long)d * 2 + 0) * NFQ + p) * NV + v) * nb + rz];
       }
-      hllc<D, T>(UL, UR, d, gamma, Fp);
+      riemann<K, D, T>(UL, UR, d, gamma, Fp);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] = fma(wq, Fp[v], acc[v]);
     }
@@ -126,17 +127,19 @@ void launch_flux(const Geo& q, int prec, const void* FS, int z0, int z1, void* F
     face_ext(q, d, z0, z1, E);
     long long nf = (long long)E[0] * E[1] * E[2];
     int blocks = grid_for(nf, 128, 152LL * 64);
-#define AWE_FLUX(D_, N_)                                                                          \
-    if (q.dim == D_ && q.N == N_) {                                                               \
+#define AWE_FLUX_K(D_, N_, K_)                                                                    \
+    if (q.dim == D_ && q.N == N_ && q.riemann == K_) {                                            \
       if (prec == AWE_FP64)                                                                       \
-        k_flux<D_, N_, double><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const double*)FS,        \
-                                                      (double*)F + off);                          \
+        k_flux<D_, N_, double, K_><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const double*)FS,    \
+                                                          (double*)F + off);                      \
       else                                                                                        \
-        k_flux<D_, N_, float><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const float*)FS,          \
-                                                     (float*)F + off);                            \
+        k_flux<D_, N_, float, K_><<<blocks, 128, 0, s>>>(q, box, d, z0, z1, (const float*)FS,      \
+                                                         (float*)F + off);                        \
     }
+#define AWE_FLUX(D_, N_) AWE_FLUX_K(D_, N_, 0) AWE_FLUX_K(D_, N_, 1) AWE_FLUX_K(D_, N_, 2) AWE_FLUX_K(D_, N_, 3)
     AWE_FLUX(2, 1) AWE_FLUX(2, 2) AWE_FLUX(2, 3) AWE_FLUX(3, 1) AWE_FLUX(3, 2) AWE_FLUX(3, 3)
 #undef AWE_FLUX
+#undef AWE_FLUX_K
     off += nf * q.nv;
   }
 }

@@ -30,6 +30,7 @@ struct Geo {
   double inflow[6][5];
   double pre[5];
   int fallback;  // positivity fallback of the face states
+  int riemann;   // awe_riemann: Riemann solver of the corrector
 };
 
 // index of an active-relative coordinate in a ghosted array
@@ -174,6 +175,132 @@ __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma,
     T Es = f * (E * ir + (Ss - u) * (Ss + p / m));
     F[D + 1] = (E + p) * u + S * (Es - E);
   }
+}
+
+// Physical flux along dir of a conserved state whose velocities, pressure
+// and energy are already known.
+template <int D, typename T>
+__device__ __forceinline__ void dir_flux(const T* U, const T* v, T p, int dir, T* F) {
+  const T un = v[dir];
+  F[0] = U[1 + dir];
+#pragma unroll
+  for (int e = 0; e < D; ++e) F[1 + e] = U[1 + e] * un;
+  F[1 + dir] += p;
+  F[D + 1] = (U[D + 1] + p) * un;
+}
+
+// HLL and HLLEM (the other solvers of Sec. I.1 besides HLLC and Rusanov).
+// HLL: the single state between the Davis-Einfeldt speeds of hllc();
+// F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) inside the fan.
+// HLLEM (EM = true): the jump term loses delta * sum_k a_k r_k over the
+// linearly degenerate Roe waves (the contact, a_c = drho - dp/c~^2,
+// r_c = (1, v~, |v~|^2/2); each shear wave t, a_t = rho~ dv_t,
+// r_t = (0, e_t, v~_t)), delta = 1 - min(u~,0)/S_L - max(u~,0)/S_R, which
+// resolves isolated contacts and shear waves exactly.
+template <int D, typename T, bool EM>
+__device__ __forceinline__ void hll_family(const T* UL, const T* UR, int dir, T gamma, T* F) {
+  constexpr int NV = D + 2;
+  const T gm1 = gamma - T(1);
+  T rl = UL[0], rr = UR[0];
+  T irl = T(1) / rl, irr = T(1) / rr;
+  T vl[D], vr[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    vl[d] = UL[1 + d] * irl;
+    vr[d] = UR[1 + d] * irr;
+  }
+  T kl = UL[1] * vl[0], kr = UR[1] * vr[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) {
+    kl = fma(UL[1 + d], vl[d], kl);
+    kr = fma(UR[1 + d], vr[d], kr);
+  }
+  T El = UL[D + 1], Er = UR[D + 1];
+  T pl = gm1 * (El - T(0.5) * kl), pr = gm1 * (Er - T(0.5) * kr);
+  T cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+  T ul = vl[dir], ur = vr[dir];
+  T sl = sqrt(rl), sr = sqrt(rr);
+  T iden = T(1) / (sl + sr);
+  T vt[D], vt2 = T(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    vt[d] = (sl * vl[d] + sr * vr[d]) * iden;
+    vt2 = fma(vt[d], vt[d], vt2);
+  }
+  T Ht = (sl * (El + pl) * irl + sr * (Er + pr) * irr) * iden;
+  T ct = sqrt(gm1 * (Ht - T(0.5) * vt2));
+  T SL = fmin(ul - cl, vt[dir] - ct);
+  T SR = fmax(ur + cr, vt[dir] + ct);
+  if (T(0) <= SL) {
+    dir_flux<D, T>(UL, vl, pl, dir, F);
+    return;
+  }
+  if (SR <= T(0)) {
+    dir_flux<D, T>(UR, vr, pr, dir, F);
+    return;
+  }
+  T FL[NV], FR[NV], jump[NV];
+  dir_flux<D, T>(UL, vl, pl, dir, FL);
+  dir_flux<D, T>(UR, vr, pr, dir, FR);
+#pragma unroll
+  for (int s = 0; s < NV; ++s) jump[s] = UR[s] - UL[s];
+  if (EM) {
+    const T ut = vt[dir];
+    const T delta = T(1) - fmin(ut, T(0)) / SL - fmax(ut, T(0)) / SR;
+    const T ac = delta * ((rr - rl) - (pr - pl) / (ct * ct));
+    jump[0] -= ac;
+#pragma unroll
+    for (int e = 0; e < D; ++e) jump[1 + e] -= ac * vt[e];
+    jump[D + 1] -= ac * (T(0.5) * vt2);
+    const T rt = sl * sr;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      if (t == dir) continue;
+      const T at = delta * (rt * (vr[t] - vl[t]));
+      jump[1 + t] -= at;
+      jump[D + 1] -= at * vt[t];
+    }
+  }
+  const T inv = T(1) / (SR - SL), slsr = SL * SR;
+#pragma unroll
+  for (int s = 0; s < NV; ++s) F[s] = (SR * FL[s] - SL * FR[s] + slsr * jump[s]) * inv;
+}
+
+// Rusanov (local Lax-Friedrichs): (F_L + F_R)/2 - S (U_R - U_L)/2 with
+// S = max(|u_L| + c_L, |u_R| + c_R), u the velocity normal to the face.
+template <int D, typename T>
+__device__ __forceinline__ void rusanov(const T* UL, const T* UR, int dir, T gamma, T* F) {
+  constexpr int NV = D + 2;
+  const T gm1 = gamma - T(1);
+  T irl = T(1) / UL[0], irr = T(1) / UR[0];
+  T vl[D], vr[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    vl[d] = UL[1 + d] * irl;
+    vr[d] = UR[1 + d] * irr;
+  }
+  T kl = UL[1] * vl[0], kr = UR[1] * vr[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) {
+    kl = fma(UL[1 + d], vl[d], kl);
+    kr = fma(UR[1 + d], vr[d], kr);
+  }
+  T pl = gm1 * (UL[D + 1] - T(0.5) * kl), pr = gm1 * (UR[D + 1] - T(0.5) * kr);
+  T S = fmax(fabs(vl[dir]) + sqrt(gamma * pl * irl), fabs(vr[dir]) + sqrt(gamma * pr * irr));
+  T FL[NV], FR[NV];
+  dir_flux<D, T>(UL, vl, pl, dir, FL);
+  dir_flux<D, T>(UR, vr, pr, dir, FR);
+#pragma unroll
+  for (int s = 0; s < NV; ++s) F[s] = T(0.5) * (FL[s] + FR[s]) - T(0.5) * S * (UR[s] - UL[s]);
+}
+
+// The corrector's Riemann solver, chosen at compile time (K = awe_riemann).
+template <int K, int D, typename T>
+__device__ __forceinline__ void riemann(const T* UL, const T* UR, int dir, T gamma, T* F) {
+  if constexpr (K == 1) hll_family<D, T, false>(UL, UR, dir, gamma, F);
+  else if constexpr (K == 2) hll_family<D, T, true>(UL, UR, dir, gamma, F);
+  else if constexpr (K == 3) rusanov<D, T>(UL, UR, dir, gamma, F);
+  else hllc<D, T>(UL, UR, dir, gamma, F);
 }
 
 // rho > 0, p > 0 and every component finite (positivity fallback test)

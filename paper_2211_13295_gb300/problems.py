@@ -52,6 +52,7 @@ class Problem:
     picard: int = 0
     seed: Optional[int] = None
     fallback: bool = False               # opt-in positivity fallback of the face states
+    riemann: str = "hllc"                # corrector's Riemann solver: hllc, hll, hllem, rusanov
     params: dict = dataclasses.field(default_factory=dict)
 
     def __post_init__(self):
