@@ -53,6 +53,9 @@ def lib():
             "ora_weno1d": (None, [C.c_int, dp, C.c_double, dp, C.c_int, dp, dp]),
             "ora_hllc": (None, [C.c_int, C.c_double, C.c_int, dp, dp, dp]),
             "ora_riemann": (None, [C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, dp]),
+            "ora_rk_coefficients": (C.c_int, [C.c_int, dp, dp]),
+            "ora_rk_rhs": (C.c_int, [cp, dp, up, dp]),
+            "ora_rk_step": (C.c_int, [cp, dp, C.c_double, C.c_double, C.c_int, C.c_int, fp, dp, dp]),
             "ora_mc_slope": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "ora_phys_flux": (None, [C.c_int, C.c_double, C.c_int, dp, dp]),
             "ora_ghosted_size": (C.c_size_t, [cp]),
@@ -86,7 +89,7 @@ def _dp(a):
 
 
 def _fp(a):
-    return a.ctypes.data_as(C.POINTER(C.c_float))
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
 
 
 def _up(a):
@@ -253,6 +256,28 @@ class Oracle:
         rc = lib().ora_step(C.byref(self.cfg), _dp(Ug), float(dt), _up(flags), _dp(out), C.byref(smax))
         return out, smax.value, rc
 
+    # --- Runge-Kutta variant -------------------------------------------
+    def rk_stages(self):
+        st = getattr(self.prob, "rk_stages", 0)
+        return st if st else {2: 2, 3: 3, 4: 5}[self.prob.order]
+
+    def rk_rhs(self, U, t, flags=None):
+        """L(U) on the active zones (ghosts filled at time t)."""
+        Ug = self.ghosted(U, t)
+        L = np.zeros((self.nv, self.n[2], self.n[1], self.n[0]))
+        lib().ora_rk_rhs(C.byref(self.cfg), _dp(Ug), _up(flags), _dp(L))
+        return L
+
+    def rk_step(self, U, t, dt, gate_params=None, nh=32, stages=None):
+        """One SSP Runge-Kutta step: returns (U_new, smax, status)."""
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.nv, self.n[2], self.n[1], self.n[0])
+        out = np.zeros_like(U)
+        smax = C.c_double()
+        gp = None if gate_params is None else np.ascontiguousarray(gate_params, dtype=np.float32)
+        rc = lib().ora_rk_step(C.byref(self.cfg), _dp(U), float(t), float(dt), int(stages or self.rk_stages()),
+                               nh, _fp(gp), _dp(out), C.byref(smax))
+        return out, smax.value, rc
+
     def signal_max(self, U):
         Ug = self.ghosted(U, 0.0)
         return lib().ora_signal_max(C.byref(self.cfg), _dp(Ug))
@@ -337,6 +362,15 @@ class Oracle:
         fl = np.zeros(Ug.shape[1:], dtype=np.uint8)
         lib().ora_gate_flags(C.byref(self.cfg), _dp(Ug), nh, _fp(params), _up(fl))
         return fl
+
+
+def rk_coefficients(stages):
+    """Shu-Osher (alpha, beta), each [stages+1][stages]."""
+    a = np.zeros((stages + 1) * stages)
+    b = np.zeros((stages + 1) * stages)
+    if lib().ora_rk_coefficients(stages, _dp(a), _dp(b)) != 0:
+        raise ValueError("stages must be 2, 3 or 5")
+    return a.reshape(stages + 1, stages), b.reshape(stages + 1, stages)
 
 
 def mlp_num_params(nin, nh=32):

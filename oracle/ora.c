@@ -1047,6 +1047,224 @@ int ora_step(const ora_cfg* c, const double* Ug, double dt, const unsigned char*
 }
 
 /* ------------------------------------------------------------------------ */
+/* Runge-Kutta variant (method of lines; Table IV's comparison scheme)        */
+/* ------------------------------------------------------------------------ */
+/* The paper compares ADER with Runge-Kutta time stepping of the same WENO
+ * reconstruction and Riemann fluxes (Sec. IV, Table IV): two stages at second
+ * order, three at third and five at fourth.  Reading: strong-stability-
+ * preserving schemes in Shu-Osher form,
+ *   U(i) = sum_{k<i} [ alpha_ik U(k) + beta_ik dt L(U(k)) ],  U(0) = U^n,
+ * with L(U) = -sum_d (F_{d,i+1/2} - F_{d,i-1/2}) / dx_d, the face fluxes the
+ * Gauss average over the face only (no time points: nq = ceil(order/2) per
+ * transverse dimension) of the Riemann solver between the reconstructed
+ * polynomials of the two zones.  Schemes: SSP(2,2) (Heun), SSP(3,3)
+ * (Shu and Osher) and the five-stage fourth-order SSP(5,4) of Spiteri and
+ * Ruuth.  The boundary values of stage k are those at time t + c_k dt, with
+ * the stage abscissae c_i = sum_k (alpha_ik c_k + beta_ik). */
+#define RK_MAXS 5
+static int rk_table(int stages, double alpha[RK_MAXS + 1][RK_MAXS], double beta[RK_MAXS + 1][RK_MAXS]) {
+  for (int i = 0; i <= RK_MAXS; ++i)
+    for (int k = 0; k < RK_MAXS; ++k) alpha[i][k] = beta[i][k] = 0.0;
+  if (stages == 2) {
+    alpha[1][0] = 1.0; beta[1][0] = 1.0;
+    alpha[2][0] = 0.5; alpha[2][1] = 0.5; beta[2][1] = 0.5;
+    return 0;
+  }
+  if (stages == 3) {
+    alpha[1][0] = 1.0; beta[1][0] = 1.0;
+    alpha[2][0] = 0.75; alpha[2][1] = 0.25; beta[2][1] = 0.25;
+    alpha[3][0] = 1.0 / 3.0; alpha[3][2] = 2.0 / 3.0; beta[3][2] = 2.0 / 3.0;
+    return 0;
+  }
+  if (stages == 5) {
+    alpha[1][0] = 1.0;               beta[1][0] = 0.391752226571890;
+    alpha[2][0] = 0.444370493651235; alpha[2][1] = 0.555629506348765; beta[2][1] = 0.368410593050371;
+    alpha[3][0] = 0.620101851488403; alpha[3][2] = 0.379898148511597; beta[3][2] = 0.251891774271694;
+    alpha[4][0] = 0.178079954393132; alpha[4][3] = 0.821920045606868; beta[4][3] = 0.544974750228521;
+    alpha[5][2] = 0.517231671970585; alpha[5][3] = 0.096059710526147; beta[5][3] = 0.063692468666290;
+    alpha[5][4] = 0.386708617503269; beta[5][4] = 0.226007483236906;
+    return 0;
+  }
+  return -1;
+}
+
+int ora_rk_coefficients(int stages, double* alpha, double* beta) {
+  double a[RK_MAXS + 1][RK_MAXS], b[RK_MAXS + 1][RK_MAXS];
+  if (rk_table(stages, a, b)) return -1;
+  for (int i = 0; i <= stages; ++i)
+    for (int k = 0; k < stages; ++k) {
+      alpha[i * stages + k] = a[i][k];
+      beta[i * stages + k] = b[i][k];
+    }
+  return 0;
+}
+
+/* L(U) on the active zones, [var][active zone], from a ghost-filled state. */
+int ora_rk_rhs(const ora_cfg* c, const double* Ug, const unsigned char* flags, double* L) {
+  geom q;
+  make_geom(c, &q);
+  const int dim = q.dim, N = q.N, nv = q.nv;
+  const int ns = ora_num_modes(dim, N);
+  int abc[MAXM * 3];
+  ora_mode_list(dim, N, abc);
+  int B[3];
+  for (int d = 0; d < 3; ++d) B[d] = d < dim ? q.n[d] + 2 : 1;
+  const size_t nbox = (size_t)B[0] * B[1] * B[2];
+  const int NQ = (c->order + 1) / 2;
+  const int np = dim == 3 ? NQ * NQ : NQ;   /* points per face, space only */
+  double* W = (double*)malloc(sizeof(double) * nv * ns * nbox);
+  double* FS = (double*)malloc(sizeof(double) * dim * 2 * np * nv * nbox);
+  ora_reconstruct(c, Ug, flags, W);
+  double xq[NQMAX], wq[NQMAX];
+  ora_gauss_legendre(NQ, xq, wq);
+  /* face states: the reconstructed polynomial at the face points */
+#pragma omp parallel for schedule(static)
+  for (long bz = 0; bz < (long)nbox; ++bz) {
+    int bad = 0;
+    for (int d = 0; d < dim; ++d) {
+      int t1 = -1, t2 = -1;
+      for (int e = 0; e < dim; ++e)
+        if (e != d) {
+          if (t1 < 0) t1 = e; else t2 = e;
+        }
+      for (int side = 0; side < 2; ++side)
+        for (int p = 0; p < np; ++p) {
+          double xi[3] = {0, 0, 0};
+          xi[d] = side ? 0.5 : -0.5;
+          xi[t1] = xq[p % NQ];
+          if (t2 >= 0) xi[t2] = xq[p / NQ];
+          double U[MAXV];
+          for (int v = 0; v < nv; ++v) {
+            double acc = 0.0;
+            for (int m = 0; m < ns; ++m) {
+              double b = 1.0;
+              for (int e = 0; e < dim; ++e) b *= ora_basis(abc[m * 3 + e], xi[e]);
+              acc += W[((size_t)v * ns + m) * nbox + bz] * b;
+            }
+            U[v] = acc;
+            FS[((((size_t)d * 2 + side) * np + p) * nv + v) * nbox + bz] = acc;
+          }
+          if (!zone_physical(&q, c->gamma, U)) bad = 1;
+        }
+    }
+    if (c->fallback && bad) {
+      for (int d = 0; d < dim; ++d)
+        for (int side = 0; side < 2; ++side)
+          for (int p = 0; p < np; ++p)
+            for (int v = 0; v < nv; ++v)
+              FS[((((size_t)d * 2 + side) * np + p) * nv + v) * nbox + bz] = W[((size_t)v * ns + 0) * nbox + bz];
+    }
+  }
+  const size_t nact = (size_t)q.n[0] * q.n[1] * q.n[2];
+  for (size_t z = 0; z < nact * nv; ++z) L[z] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    int E[3] = {q.n[0], q.n[1], q.n[2]};
+    E[d] += 1;
+    size_t nf = (size_t)E[0] * E[1] * E[2];
+    double* F = (double*)malloc(sizeof(double) * nv * nf);
+#pragma omp parallel for schedule(static)
+    for (long f = 0; f < (long)nf; ++f) {
+      int fi[3] = {(int)(f % E[0]), (int)((f / E[0]) % E[1]), (int)(f / ((size_t)E[0] * E[1]))};
+      int lb[3], rb[3];
+      for (int e = 0; e < 3; ++e) lb[e] = rb[e] = e < dim ? fi[e] + 1 : 0;
+      lb[d] -= 1;
+      size_t lz = ((size_t)lb[2] * B[1] + lb[1]) * B[0] + lb[0];
+      size_t rz = ((size_t)rb[2] * B[1] + rb[1]) * B[0] + rb[0];
+      double acc[MAXV] = {0, 0, 0, 0, 0};
+      for (int p = 0; p < np; ++p) {
+        double wt = wq[p % NQ] * (dim == 3 ? wq[p / NQ] : 1.0);
+        double UL[MAXV], UR[MAXV], Fp[MAXV];
+        for (int v = 0; v < nv; ++v) {
+          UL[v] = FS[((((size_t)d * 2 + 1) * np + p) * nv + v) * nbox + lz];
+          UR[v] = FS[((((size_t)d * 2 + 0) * np + p) * nv + v) * nbox + rz];
+        }
+        ora_riemann(c->riemann, dim, c->gamma, d, UL, UR, Fp);
+        for (int v = 0; v < nv; ++v) acc[v] += wt * Fp[v];
+      }
+      for (int v = 0; v < nv; ++v) F[(size_t)v * nf + f] = acc[v];
+    }
+    for (size_t z = 0; z < nact; ++z) {
+      int i = (int)(z % q.n[0]), j = (int)((z / q.n[0]) % q.n[1]), k = (int)(z / ((size_t)q.n[0] * q.n[1]));
+      int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+      hi[d] += 1;
+      size_t fl = ((size_t)lo[2] * E[1] + lo[1]) * E[0] + lo[0];
+      size_t fh = ((size_t)hi[2] * E[1] + hi[1]) * E[0] + hi[0];
+      for (int v = 0; v < nv; ++v) L[(size_t)v * nact + z] -= (F[(size_t)v * nf + fh] - F[(size_t)v * nf + fl]) / q.dx[d];
+    }
+    free(F);
+  }
+  free(W);
+  free(FS);
+  return 0;
+}
+
+/* One Runge-Kutta step from the active state U at time t (ghost zones are
+ * filled by the boundary conditions at each stage's time); gate_params, if
+ * not NULL, are the MLP weights (nh hidden units) from which each stage
+ * computes its troubled-zone flags.  Returns -4 if a stage state or the
+ * result is non-physical, -1 for an unknown stage count. */
+int ora_rk_step(const ora_cfg* c, const double* U, double t, double dt, int stages, int nh,
+                const float* gate_params, double* Uout, double* smax) {
+  double alpha[RK_MAXS + 1][RK_MAXS], beta[RK_MAXS + 1][RK_MAXS];
+  if (rk_table(stages, alpha, beta)) return -1;
+  geom q;
+  make_geom(c, &q);
+  const int nv = q.nv, dim = q.dim;
+  const size_t nact = (size_t)q.n[0] * q.n[1] * q.n[2];
+  double* Us[RK_MAXS + 1];
+  double* Ls[RK_MAXS];
+  double cst[RK_MAXS + 1];
+  for (int i = 0; i <= stages; ++i) Us[i] = (double*)malloc(sizeof(double) * nv * nact);
+  for (int i = 0; i < stages; ++i) Ls[i] = (double*)malloc(sizeof(double) * nv * nact);
+  double* Ug = (double*)malloc(sizeof(double) * nv * q.ntot);
+  unsigned char* flags = gate_params ? (unsigned char*)malloc(q.ntot) : NULL;
+  memcpy(Us[0], U, sizeof(double) * nv * nact);
+  cst[0] = 0.0;
+  int bad = 0;
+  for (int i = 1; i <= stages; ++i) {
+    /* L of the previous stage */
+    const int k = i - 1;
+    for (size_t z = 0; z < q.ntot * nv; ++z) Ug[z] = 0.0;
+    for (size_t z = 0; z < nact; ++z) {
+      int a = (int)(z % q.n[0]), b = (int)((z / q.n[0]) % q.n[1]), cc = (int)(z / ((size_t)q.n[0] * q.n[1]));
+      size_t gz = gidx(&q, a + q.g, b + q.g, dim == 3 ? cc + q.g : 0);
+      for (int v = 0; v < nv; ++v) Ug[(size_t)v * q.ntot + gz] = Us[k][(size_t)v * nact + z];
+    }
+    ora_fill_ghosts(c, Ug, t + cst[k] * dt);
+    if (flags) ora_gate_flags(c, Ug, nh, gate_params, flags);
+    ora_rk_rhs(c, Ug, flags, Ls[k]);
+    /* stage i */
+    cst[i] = 0.0;
+    for (int kk = 0; kk < i; ++kk) cst[i] += alpha[i][kk] * cst[kk] + beta[i][kk];
+    for (size_t z = 0; z < nact; ++z) {
+      double Uz[MAXV];
+      for (int v = 0; v < nv; ++v) {
+        double acc = 0.0;
+        for (int kk = 0; kk < i; ++kk)
+          acc += alpha[i][kk] * Us[kk][(size_t)v * nact + z] + beta[i][kk] * dt * Ls[kk][(size_t)v * nact + z];
+        Us[i][(size_t)v * nact + z] = acc;
+        Uz[v] = acc;
+      }
+      if (!zone_physical(&q, c->gamma, Uz)) bad = 1;
+    }
+  }
+  double sm = 0.0;
+  for (size_t z = 0; z < nact; ++z) {
+    double Uz[MAXV];
+    for (int v = 0; v < nv; ++v) Uz[v] = Us[stages][(size_t)v * nact + z];
+    double sg = zone_signal(&q, c->gamma, Uz);
+    if (sg > sm) sm = sg;
+  }
+  memcpy(Uout, Us[stages], sizeof(double) * nv * nact);
+  if (smax) *smax = sm;
+  for (int i = 0; i <= stages; ++i) free(Us[i]);
+  for (int i = 0; i < stages; ++i) free(Ls[i]);
+  free(Ug);
+  free(flags);
+  return bad ? -4 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact Riemann solver (ideal gas), from the wave curves of the Euler       */
 /* equations: shock branch from Rankine-Hugoniot, rarefaction branch from the */
 /* isentropic Riemann invariant; p* by Newton's method on the pressure        */

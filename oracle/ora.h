@@ -86,6 +86,14 @@ int ora_step(const ora_cfg* c, const double* Ug, double dt, const unsigned char*
 /* Face-averaged fluxes of active faces: F[dir][var][face], face grid (n_d+1) along dir. */
 int ora_fluxes(const ora_cfg* c, const double* Ug, const unsigned char* flags, double dt, double* F);
 double ora_signal_max(const ora_cfg* c, const double* Ug);
+/* Runge-Kutta variant (Table IV's comparison scheme; see ora.c): Shu-Osher
+ * coefficients of the SSP scheme with 2, 3 or 5 stages ([stages+1][stages],
+ * row i = stage i), L(U) of a ghost-filled state on the active zones, and
+ * one whole step from an active state at time t. */
+int ora_rk_coefficients(int stages, double* alpha, double* beta);
+int ora_rk_rhs(const ora_cfg* c, const double* Ug, const unsigned char* flags, double* L);
+int ora_rk_step(const ora_cfg* c, const double* U, double t, double dt, int stages, int nh,
+                const float* gate_params, double* Uout, double* smax);
 
 /* ---- exact Riemann solver (ideal gas) sampled at x/t = s ---- */
 int ora_exact_riemann(double gamma, double rl, double ul, double pl,

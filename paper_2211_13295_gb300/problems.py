@@ -53,6 +53,8 @@ class Problem:
     seed: Optional[int] = None
     fallback: bool = False               # opt-in positivity fallback of the face states
     riemann: str = "hllc"                # corrector's Riemann solver: hllc, hll, hllem, rusanov
+    scheme: str = "ader"                 # time stepping: ader, or ssprk (Table IV's comparison)
+    rk_stages: int = 0                   # SSP-RK stages (2, 3, 5); 0: 2, 3, 5 at orders 2, 3, 4
     params: dict = dataclasses.field(default_factory=dict)
 
     def __post_init__(self):
