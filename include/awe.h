@@ -80,6 +80,17 @@ typedef enum {
   AWE_RS_RUSANOV = 3
 } awe_riemann;
 
+/* Time stepping.  ADER: the paper's one-step predictor-corrector.  SSPRK: the
+ * Runge-Kutta comparison scheme of Table IV (method of lines with the same
+ * reconstruction and Riemann fluxes, face fluxes averaged over the face
+ * Gauss points only): SSP(2,2), SSP(3,3) or Spiteri and Ruuth's five-stage
+ * SSP(5,4) in Shu-Osher form, stage boundary values at t + c_i dt.  The
+ * probes (awe_probe_*) cover the ADER path only. */
+typedef enum {
+  AWE_SCHEME_ADER = 0,
+  AWE_SCHEME_SSPRK = 1
+} awe_scheme;
+
 typedef struct {
   int dim;               /* 2 or 3 */
   int n[3];              /* active zones per dimension (n[2] ignored in 2D) */
@@ -105,6 +116,9 @@ typedef struct {
                             non-finite value uses its zone mean as every face
                             state (first order) */
   int riemann;           /* awe_riemann: the corrector's Riemann solver */
+  int scheme;            /* awe_scheme: ADER (default) or SSP Runge-Kutta */
+  int rk_stages;         /* AWE_SCHEME_SSPRK: 2, 3 or 5 stages (0: 2, 3, 5 at
+                            orders 2, 3, 4, as in Table IV) */
 } awe_config;
 
 /* Create a grid (allocates all device memory).  Cites: Fig. 1 data region.

@@ -25,6 +25,7 @@ AWE_OK, AWE_ERR_ARG, AWE_ERR_CUDA, AWE_ERR_OOM, AWE_ERR_NONPHYSICAL, AWE_ERR_TIM
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "inflow": 3, "dmr_bottom": 4, "dmr_top": 5}
 PREC = {"fp64": 0, "fp32": 1}
 RIEMANN = {"hllc": 0, "hll": 1, "hllem": 2, "rusanov": 3}
+SCHEME = {"ader": 0, "ssprk": 1}
 
 
 class AweError(RuntimeError):
@@ -40,7 +41,7 @@ class AweConfig(C.Structure):
         ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5), ("prec", C.c_int),
         ("picard", C.c_int), ("weno_eps", C.c_double), ("lin", C.c_double * 4), ("cfl", C.c_double),
         ("gate", C.c_int), ("slab", C.c_int), ("fallback", C.c_int),
-        ("riemann", C.c_int),
+        ("riemann", C.c_int), ("scheme", C.c_int), ("rk_stages", C.c_int),
     ]
 
 
@@ -162,6 +163,8 @@ def make_config(prob, prec="fp64", gate=False, slab=0, cfl=None, picard=None) ->
     c.slab = slab
     c.fallback = 1 if getattr(prob, "fallback", False) else 0
     c.riemann = RIEMANN[getattr(prob, "riemann", "hllc")]
+    c.scheme = SCHEME[getattr(prob, "scheme", "ader")]
+    c.rk_stages = int(getattr(prob, "rk_stages", 0))
     return c
 
 

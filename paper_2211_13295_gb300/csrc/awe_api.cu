@@ -20,6 +20,7 @@
 
 #include "awe_gate.h"
 #include "awe_internal.cuh"
+#include "awe_rk.h"
 #include "awe_tables.h"
 
 namespace awe {
@@ -33,9 +34,9 @@ using namespace awe;
 
 namespace {
 
-enum Kind { K_GHOST = 0, K_RX, K_RY, K_RZ, K_PRED, K_FLUX, K_UPD, K_GATE, K_MISC, K_COUNT };
+enum Kind { K_GHOST = 0, K_RX, K_RY, K_RZ, K_PRED, K_FLUX, K_UPD, K_GATE, K_MISC, K_FACE, K_COUNT };
 const char* kKindNames[K_COUNT] = {"fill_ghosts", "recon_x", "recon_y", "recon_z", "predictor",
-                                   "hllc_flux", "update_cfl", "gate", "misc"};
+                                   "riemann_flux", "update_cfl", "gate", "misc", "face_eval"};
 
 struct Prof {
   bool on = false;
@@ -62,6 +63,8 @@ struct awe_grid {
   int* d_err = nullptr;
   void *X = nullptr, *Y = nullptr, *XY = nullptr, *W = nullptr, *FS = nullptr, *F = nullptr;
   double* stage = nullptr;  // state staging [nv][nact]
+  double* Urk[2] = {nullptr, nullptr};  // Runge-Kutta stage states (ghosted)
+  awe::RKScheme rk;
   void* ptab = nullptr;
   PTabLayout L;
   size_t bytesT = 8;
@@ -236,20 +239,129 @@ void run_slab(awe_grid* g, int z0, int z1, bool do_flux, bool do_update, const u
   prof_span(g, K_UPD, m3, m4);
 }
 
-void fill_ghosts(awe_grid* g) {
+void fill_ghosts(awe_grid* g, double* U = nullptr, double c = 0.0) {
   int a = prof_mark(g);
-  launch_fill_ghosts(g->q, g->U[g->cur], g->d_scal + 0, g->s);
+  launch_fill_ghosts(g->q, U ? U : g->U[g->cur], g->d_scal + 0, g->d_scal + 1, c, g->s);
   int b = prof_mark(g);
   prof_span(g, K_GHOST, a, b);
 }
 
-const unsigned char* gate_flags_for_step(awe_grid* g) {
+const unsigned char* gate_flags_for_step(awe_grid* g, const double* U = nullptr) {
   if (!g->cfg.gate) return nullptr;
   int a = prof_mark(g);
-  const unsigned char* f = awe::gate_compute_flags(g->gate, g->q, g->prec, g->U[g->cur], g->s);
+  const unsigned char* f = awe::gate_compute_flags(g->gate, g->q, g->prec, U ? U : g->U[g->cur], g->s);
   int b = prof_mark(g);
   prof_span(g, K_GATE, a, b);
   return f;
+}
+
+// the Runge-Kutta stage pipeline of one slab: recon of the stage input,
+// face values, fluxes, stage combination
+void run_slab_rk(awe_grid* g, const double* in, int z0, int z1, const unsigned char* flags,
+                 const RKOut& o1, const RKOut& o2, int nout, bool last) {
+  const Geo& q = g->q;
+  int m0 = prof_mark(g);
+  cudaEvent_t evs[3];
+  cudaEvent_t* ev = nullptr;
+  int mi[3] = {-1, -1, -1};
+  if (g->prof.on) {
+    for (int k = 0; k < 3; ++k) {
+      evs[k] = prof_event(g);
+      mi[k] = (int)g->prof.used - 1;
+    }
+    ev = evs;
+  }
+  launch_recon(q, g->prec, in, flags, z0, z1, g->X, g->Y, g->XY, g->W, g->s, ev);
+  prof_span(g, K_RX, m0, mi[0]);
+  prof_span(g, K_RY, mi[0], mi[1]);
+  if (q.dim == 3) prof_span(g, K_RZ, mi[1], mi[2]);
+  int m1 = q.dim == 3 ? mi[2] : mi[1];
+  launch_face_eval(q, g->prec, g->W, z0, z1, g->ptab, g->L, g->FS, g->s);
+  int m2 = prof_mark(g);
+  prof_span(g, K_FACE, m1, m2);
+  launch_rk_flux(q, g->prec, g->FS, z0, z1, g->F, g->s);
+  int m3 = prof_mark(g);
+  prof_span(g, K_FLUX, m2, m3);
+  launch_rk_update(q, g->prec, g->U[g->cur], in, g->F, g->d_scal + 1, z0, z1, o1, o2, nout,
+                   last ? g->d_smax : nullptr, g->d_err, g->s);
+  int m4 = prof_mark(g);
+  prof_span(g, K_UPD, m3, m4);
+}
+
+// Stage plan of a Shu-Osher scheme: at stage input k, the outputs are the
+// stages i > k with alpha_ik or beta_ik nonzero (k = 0: beta_i0 nonzero, or
+// i = 1); a stage's U(0) term alpha_i0 U(0) enters with its first output.
+// Buffers: U(0) is the current state, the last stage the other state buffer,
+// the others come from the two Runge-Kutta buffers and return there once
+// their stage has served as input.  Returns false if a plan needs more than
+// two outputs per input or more than two buffers.
+struct RKPlan {
+  int nout[kRKMax];
+  int stage[kRKMax][2];
+  int buf[kRKMax + 1];  // -1: U(0); 0, 1: Urk; 2: the output state
+};
+bool rk_plan(const RKScheme& r, RKPlan& p) {
+  bool started[kRKMax + 1] = {false};
+  bool used[2] = {false, false};
+  p.buf[0] = -1;
+  for (int i = 1; i <= r.s; ++i) p.buf[i] = -2;
+  for (int k = 0; k < r.s; ++k) {
+    p.nout[k] = 0;
+    for (int i = k + 1; i <= r.s; ++i) {
+      bool contrib = k == 0 ? (i == 1 || r.beta[i][0] != 0.0) : (r.alpha[i][k] != 0.0 || r.beta[i][k] != 0.0);
+      if (!contrib) continue;
+      if (p.nout[k] == 2) return false;
+      if (!started[i]) {
+        if (i == r.s) {
+          p.buf[i] = 2;
+        } else {
+          int b = !used[0] ? 0 : !used[1] ? 1 : -1;
+          if (b < 0) return false;
+          used[b] = true;
+          p.buf[i] = b;
+        }
+        started[i] = true;
+      }
+      p.stage[k][p.nout[k]++] = i;
+    }
+    // the stage completed here comes first
+    if (p.nout[k] == 0 || p.stage[k][0] != k + 1) {
+      if (p.nout[k] == 2 && p.stage[k][1] == k + 1) std::swap(p.stage[k][0], p.stage[k][1]);
+      else return false;
+    }
+    if (k >= 1 && p.buf[k] >= 0 && p.buf[k] < 2) used[p.buf[k]] = false;
+  }
+  return true;
+}
+
+int rk_step(awe_grid* g) {
+  const RKScheme& r = g->rk;
+  RKPlan p;
+  if (!rk_plan(r, p)) return fail(g, AWE_ERR_STATE, "Runge-Kutta stage plan");
+  auto bufp = [&](int b) { return b == -1 ? g->U[g->cur] : b == 2 ? g->U[1 - g->cur] : g->Urk[b]; };
+  bool started[kRKMax + 1] = {false};
+  for (int k = 0; k < r.s; ++k) {
+    double* in = bufp(p.buf[k]);
+    fill_ghosts(g, in, r.c[k]);
+    const unsigned char* flags = gate_flags_for_step(g, in);
+    RKOut o[2];
+    for (int j = 0; j < p.nout[k]; ++j) {
+      int i = p.stage[k][j];
+      o[j].out = bufp(p.buf[i]);
+      o[j].init = started[i] ? 0 : 1;
+      o[j].a0 = r.alpha[i][0];
+      o[j].al = k == 0 ? 0.0 : r.alpha[i][k];
+      o[j].be = r.beta[i][k];
+      started[i] = true;
+    }
+    if (p.nout[k] < 2) o[1] = o[0];
+    for (int sidx = 0; sidx < nslabs(g); ++sidx) {
+      int z0, z1;
+      slab_range(g, sidx, z0, z1);
+      run_slab_rk(g, in, z0, z1, flags, o[0], o[1], p.nout[k], k == r.s - 1);
+    }
+  }
+  return AWE_OK;
 }
 
 }  // namespace
@@ -280,6 +392,10 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   if (c.slab < 0) return fail(nullptr, AWE_ERR_ARG, "negative slab");
   if (c.riemann < AWE_RS_HLLC || c.riemann > AWE_RS_RUSANOV)
     return fail(nullptr, AWE_ERR_ARG, "riemann must be one of AWE_RS_HLLC, AWE_RS_HLL, AWE_RS_HLLEM, AWE_RS_RUSANOV");
+  if (c.scheme != AWE_SCHEME_ADER && c.scheme != AWE_SCHEME_SSPRK)
+    return fail(nullptr, AWE_ERR_ARG, "scheme must be AWE_SCHEME_ADER or AWE_SCHEME_SSPRK");
+  if (c.scheme == AWE_SCHEME_SSPRK && c.rk_stages != 0 && c.rk_stages != 2 && c.rk_stages != 3 && c.rk_stages != 5)
+    return fail(nullptr, AWE_ERR_ARG, "rk_stages must be 0, 2, 3 or 5");
   if (c.dim == 3 && c.n[0] * (long long)c.n[1] * c.n[2] > (1LL << 31))
     return fail(nullptr, AWE_ERR_ARG, "grid too large");
   const char* forced = std::getenv("AWE_FAIL_ALLOC");
@@ -315,6 +431,14 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   for (int v = 0; v < 5; ++v) q.pre[v] = c.pre[v];
   q.fallback = c.fallback ? 1 : 0;
   q.riemann = c.riemann;
+  if (c.scheme == AWE_SCHEME_SSPRK) {
+    int st = c.rk_stages ? c.rk_stages : (c.order == 2 ? 2 : c.order == 3 ? 3 : 5);
+    RKPlan plan;
+    if (!rk_scheme(st, g->rk) || !rk_plan(g->rk, plan)) {
+      delete g;
+      return fail(nullptr, AWE_ERR_ARG, "no Runge-Kutta scheme with that stage count");
+    }
+  }
   g->slab = (c.dim == 3 && c.slab > 0 && c.slab < c.n[2]) ? c.slab : q.n[2];
   if (c.dim == 2) g->slab = 1;
   g->bytesT = tsize(c.prec);
@@ -346,6 +470,10 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
       {&g->F, g->bytesT * sz.F, "fluxes"},
       {(void**)&g->stage, sizeof(double) * q.nv * nactive(q), "staging"},
   };
+  if (c.scheme == AWE_SCHEME_SSPRK) {
+    allocs.push_back({(void**)&g->Urk[0], nbytesU, "Runge-Kutta stage state"});
+    allocs.push_back({(void**)&g->Urk[1], nbytesU, "Runge-Kutta stage state"});
+  }
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) {
@@ -371,6 +499,8 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(g->U[0], 0, nbytesU, g->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->U[1], 0, nbytesU, g->s);
+  for (int b = 0; b < 2; ++b)
+    if (e == cudaSuccess && g->Urk[b]) e = cudaMemsetAsync(g->Urk[b], 0, nbytesU, g->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_scal, 0, 4 * sizeof(double), g->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_smax, 0, sizeof(unsigned long long), g->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->s);
@@ -393,7 +523,8 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
 int awe_destroy(awe_grid* g) {
   if (!g) return AWE_OK;
   cudaStreamSynchronize(g->s);
-  void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax, g->d_err, g->X, g->Y, g->XY, g->W, g->FS, g->F, g->stage, g->ptab};
+  void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax, g->d_err, g->X,     g->Y,     g->XY,
+                  g->W,    g->FS,   g->F,      g->stage,  g->ptab,  g->Urk[0], g->Urk[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   awe::gate_free(g->gate);
@@ -468,12 +599,17 @@ int awe_step(awe_grid* g, double dt, double* dt_next_out) {
   if (!g) return AWE_ERR_ARG;
   if (g->cfg.gate && !g->gate.have_weights) return fail(g, AWE_ERR_STATE, "gate enabled without weights");
   if (dt > 0) launch_set_scalar(g->d_scal + 1, dt, g->s);
-  fill_ghosts(g);
-  const unsigned char* flags = gate_flags_for_step(g);
-  for (int sidx = 0; sidx < nslabs(g); ++sidx) {
-    int z0, z1;
-    slab_range(g, sidx, z0, z1);
-    run_slab(g, z0, z1, true, true, flags);
+  if (g->cfg.scheme == AWE_SCHEME_SSPRK) {
+    int rc = rk_step(g);
+    if (rc != AWE_OK) return rc;
+  } else {
+    fill_ghosts(g);
+    const unsigned char* flags = gate_flags_for_step(g);
+    for (int sidx = 0; sidx < nslabs(g); ++sidx) {
+      int z0, z1;
+      slab_range(g, sidx, z0, z1);
+      run_slab(g, z0, z1, true, true, flags);
+    }
   }
   launch_finalize(g->q, g->d_scal + 0, g->d_scal + 1, g->d_smax, 1, g->s);
   g->cur = 1 - g->cur;
@@ -500,6 +636,8 @@ int awe_check(awe_grid* g) {
 // ---- probes ------------------------------------------------------------------
 static int probe_prepare(awe_grid* g, double dt, bool set_dt) {
   if (nslabs(g) != 1) return fail(g, AWE_ERR_STATE, "probes need a single-slab grid");
+  if (set_dt && g->cfg.scheme != AWE_SCHEME_ADER)
+    return fail(g, AWE_ERR_STATE, "the face-state and flux probes cover the ADER scheme");
   if (set_dt) {
     CK(g, cudaMemcpyAsync(g->d_scal + 2, g->d_scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
     launch_set_scalar(g->d_scal + 1, dt, g->s);

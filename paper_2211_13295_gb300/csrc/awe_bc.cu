@@ -9,9 +9,12 @@ namespace awe {
 // corner ghost is the z-image of the y-image of the x-image.  Resolved here
 // from the outermost dimension inwards; reflections accumulate sign flips of
 // the normal momentum, a fixed state ends the chain.
-__global__ void k_fill_ghosts(Geo q, double* __restrict__ U, const double* __restrict__ d_t) {
+__global__ void k_fill_ghosts(Geo q, double* __restrict__ U, const double* __restrict__ d_t,
+                              const double* __restrict__ d_dt, double c) {
   const long long total = q.ntot;
-  const double t = *d_t;
+  // time of the boundary values: t, or a Runge-Kutta stage's t + c dt
+  // (rounded as written: no contraction into an FMA)
+  const double t = c != 0.0 ? __dadd_rn(*d_t, __dmul_rn(c, *d_dt)) : *d_t;
   for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < total;
        z += (long long)gridDim.x * blockDim.x) {
     int gi = (int)(z % q.G[0]);
@@ -65,12 +68,13 @@ __global__ void k_fill_ghosts(Geo q, double* __restrict__ U, const double* __res
   }
 }
 
-void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, cudaStream_t s) {
+void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, const double* d_dt, double c,
+                        cudaStream_t s) {
   long long total = q.ntot;
   int threads = 256;
   long long blocks = (total + threads - 1) / threads;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  k_fill_ghosts<<<(int)blocks, threads, 0, s>>>(q, U, d_t);
+  k_fill_ghosts<<<(int)blocks, threads, 0, s>>>(q, U, d_t, d_dt, c);
 }
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }

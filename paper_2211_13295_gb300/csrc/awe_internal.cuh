@@ -468,7 +468,9 @@ static inline cudaError_t upload_local_tables(cudaStream_t s) {
 struct Bufs;  // defined in awe_api.cu
 
 
-void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, cudaStream_t s);
+// ghost zones of U at time *d_t + c * *d_dt (c = 0: *d_t; d_dt may then be null)
+void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, const double* d_dt, double c,
+                        cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 void launch_signal_max(const Geo& q, const double* U, unsigned long long* smax, int* err,
                        cudaStream_t s);
