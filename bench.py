@@ -227,15 +227,16 @@ def cpu_baseline_and_parity(prob, grid_state_after, U0, dt0, n_windows=3, m=4, s
     return base, parity
 
 
-def orders_192(args, world):
+def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
     """Zone-updates/s of the FP64 form at orders 2, 3 and 4 on a 192^3
-    Taylor-Green grid: the grid of the paper's Table II (whose A100 numbers
-    were measured on an unnamed problem; context only)."""
+    Taylor-Green grid: the grid of the paper's Tables II and IV (whose A100
+    numbers were measured on an unnamed problem; context only).  scheme
+    "ssprk" is Table IV's Runge-Kutta comparison (2, 3, 5 stages)."""
     from paper_2211_13295_gb300 import awe
     from paper_2211_13295_gb300 import problems as P
     out = {}
-    for order in (2, 3, 4):
-        prob = P.tgv3d(n=192, order=order, cfl=0.3)
+    for order in orders:
+        prob = P.tgv3d(n=192, order=order, cfl=0.3).replace(scheme=scheme, riemann=riemann)
         g = awe.Grid(prob)
         g.set_state(prob.initial_state())
         ms, _ = time_steps(g, 3, 3, world)
@@ -355,9 +356,11 @@ def run_native(args, rank, world, local):
     if not args.no_forms and args.form == "fp64":
         forms.update(gated_forms(args, prob, Uh, U1, zones, world))
 
-    table2 = None
+    table2 = table4 = solvers = None
     if not args.no_forms and args.form == "fp64":
         table2 = orders_192(args, world)
+        table4 = orders_192(args, world, scheme="ssprk")
+        solvers = {k: orders_192(args, world, riemann=k, orders=(4,))["O4"] for k in ("hll", "hllem", "rusanov")}
 
     cpu = None
     parity = None
@@ -396,6 +399,8 @@ def run_native(args, rank, world, local):
             "cpu_baseline": cpu,
             "forms": forms,
             "orders_tgv192_fp64": table2,
+            "ssprk_orders_tgv192_fp64": table4,
+            "riemann_tgv192_o4_fp64": solvers,
         }
         print(json.dumps(line))
 

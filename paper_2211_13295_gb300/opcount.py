@@ -162,7 +162,7 @@ def step_flops_per_zone(prob, picard=None, gate_linear_fraction=0.0):
     out["predictor"] = (pf * box / nact, pd * box / nact)
     ff, fd = flux_flops(D, N)
     nfaces = sum((n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)) for d in range(D))
-    out["hllc_flux"] = (ff * nfaces / nact, fd * nfaces / nact)
+    out["riemann_flux"] = (ff * nfaces / nact, fd * nfaces / nact)
     uf, ud = update_flops(D)
     out["update_cfl"] = (uf, ud)
     return out

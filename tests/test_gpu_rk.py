@@ -97,9 +97,11 @@ def test_time_dependent_boundary_at_the_stage_times(awe, stages):
 
 
 def test_gate_flags_every_stage(awe):
-    """Gated reconstruction with flags recomputed from each stage's state."""
+    """Gated reconstruction with flags recomputed from each stage's state
+    (smooth data: with these random weights the shocked case loses
+    positivity in the oracle as well)."""
     from paper_2211_13295_gb300.gate_train import he_init
-    prob, U = make(3, 4, (7, 6, 5), "shock")
+    prob, U = make(3, 4, (7, 6, 5), "smooth")
     prob = prob.replace(scheme="ssprk")
     nin, _ = awe.gate_dims(3, 4)
     params = he_init(nin, 7)
