@@ -16,6 +16,18 @@ __host__ __device__ __forceinline__ void face_ext(const Geo& q, int d, int z0, i
   E[2] = (q.dim == 3 ? z1 - z0 : 1) + (d == 2);
 }
 
+// The states are read rotated so that the momentum normal to the face is
+// component 1 (then the tangential ones in order of their dimension): the
+// Riemann solver runs with a compile-time direction and keeps its arrays in
+// registers.  rotated_var gives the stored variable of rotated component r.
+template <int D>
+__host__ __device__ __forceinline__ int rotated_var(int r, int d) {
+  if (r == 0 || r == D + 1) return r;
+  if (r == 1) return 1 + d;
+  if (r == 2) return d == 0 ? 2 : 1;
+  return d == 2 ? 2 : 3;  // r == 3 (3D)
+}
+
 template <int D, int N, typename T, int K, int NP>
 __global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, int z1,
                                               const T* __restrict__ FS, T* __restrict__ F) {
@@ -37,20 +49,23 @@ __global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, 
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
-#pragma unroll
+    // (HLLEM's restored waves hold more live values: unrolling all its points
+    // spills in FP64)
+#pragma unroll (K == 2 ? 2 : NFQ)
     for (int p = 0; p < NFQ; ++p) {
       T UL[NV], UR[NV], Fp[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        UL[v] = FS[((((long long)d * 2 + 1) * NFQ + p) * NV + v) * nb + lz];
-        UR[v] = FS[((((long long)d * 2 + 0) * NFQ + p) * NV + v) * nb + rz];
+      for (int r = 0; r < NV; ++r) {
+        const int v = rotated_var<D>(r, d);
+        UL[r] = FS[((((long long)d * 2 + 1) * NFQ + p) * NV + v) * nb + lz];
+        UR[r] = FS[((((long long)d * 2 + 0) * NFQ + p) * NV + v) * nb + rz];
       }
-      riemann<K, D, T>(UL, UR, d, gamma, Fp);
+      riemann<K, D, T>(UL, UR, 0, gamma, Fp);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = fma(wq, Fp[v], acc[v]);
+      for (int r = 0; r < NV; ++r) acc[r] = fma(wq, Fp[r], acc[r]);
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[(long long)v * nf + f] = acc[v];
+    for (int r = 0; r < NV; ++r) F[(long long)rotated_var<D>(r, d) * nf + f] = acc[r];
   }
 }
 

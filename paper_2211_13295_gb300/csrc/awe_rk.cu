@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) k_face_eval(Geo q, Region box, const T* _
       T w[NS];
 #pragma unroll
       for (int m = 0; m < NS; ++m) w[m] = W[((long long)v * NS + m) * nb + r];
-#pragma unroll
+#pragma unroll 2
       for (int row = 0; row < NR; ++row) {
         T acc = T(0);
 #pragma unroll
