@@ -239,10 +239,12 @@ def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
         prob = P.tgv3d(n=192, order=order, cfl=0.3).replace(scheme=scheme, riemann=riemann)
         g = awe.Grid(prob)
         g.set_state(prob.initial_state())
-        ms, _ = time_steps(g, 3, 3, world)
+        ms, prof = time_steps(g, 3, 3, world)
         ms = max_over_ranks(ms, world)
         g.close()
         out[f"O{order}"] = world * prob.zones * 3 / (ms * 1e-3)
+        if scheme != "ader" and order == 4:
+            out["O4_stage_ms_per_step"] = {k: v[1] / 3 for k, v in prof.items() if v[0]}
     return out
 
 
@@ -257,10 +259,13 @@ def gated_forms(args, prob, Uh, U1, zones, world):
     probs = [P.blast3d(n=48, order=4).replace(fallback=True), P.kh3d(n=48, order=4),
              P.tgv3d(n=48, order=4, cfl=0.3)]
     X, Y = gate_train.collect(probs, steps=(0, 3, 8))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     nin = X.shape[1]
     params, loss = gate_train.train(X, Y, nin, steps=1500, batch=8192)
     acc, recall, frac = gate_train.accuracy(params, X, Y, nin)
-    train_s = time.perf_counter() - t0
+    t2 = time.perf_counter()
+    collect_s, train_s = t1 - t0, t2 - t1
     out = {}
     for prec in ("fp64", "fp32"):
         g = awe.Grid(prob, prec=prec, gate=True)
@@ -282,7 +287,8 @@ def gated_forms(args, prob, Uh, U1, zones, world):
                 float(np.abs(Ug1[v] - U1[v]).sum() / max(np.abs(U1[v]).sum(), sc)) for v in range(5))
         out[f"{prec}_gated"] = d
     out["gate_training"] = {"rows": int(X.shape[0]), "positive_fraction": float(Y.mean()),
-                            "accuracy": acc, "recall": recall, "seconds": train_s,
+                            "accuracy": acc, "recall": recall, "train_seconds": train_s,
+                            "collect_seconds": collect_s,
                             "final_loss": float(loss[-50:].mean())}
     return out
 
