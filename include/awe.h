@@ -10,7 +10,10 @@
  * extends them in time (Predictor, Fig. 4), HLLC Riemann fluxes at
  * space-time quadrature points of every face (Make_Flux_X/Y/Z, Fig. 5), the
  * conservative update (Make_dU_dt, Fig. 6) and the CFL reduction of the next
- * time step (Update_U_Timestep, Fig. 7).  The state stays resident in device
+ * time step (Update_U_Timestep, Fig. 7).  Per grid it also offers the paper's
+ * own second-order scheme (order 2), the HLL, HLLEM and Rusanov solvers in
+ * place of HLLC (Sec. I.1), and the Runge-Kutta time stepping that Table IV
+ * compares ADER with (AWE_SCHEME_SSPRK).  The state stays resident in device
  * memory between steps (the paper's U_skinny lesson, Sec. II.2, Tables I-II);
  * it crosses to the host only through awe_set_state / awe_get_state.
  *
@@ -147,9 +150,12 @@ int awe_get_time(awe_grid* g, double* t);
  * device-resident dt used by awe_step(g, 0, ...).  Synchronises if dt_out. */
 int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out);
 
-/* One full ADER-WENO step (Fig. 1 loop body): ghost zones, reconstruction,
- * predictor, HLLC face fluxes with space-time quadrature, FP64 update, and
- * the CFL reduction of the updated state.  dt > 0: use it; dt <= 0: use the
+/* One full step.  ADER (Fig. 1 loop body): ghost zones, reconstruction,
+ * predictor, Riemann fluxes (cfg.riemann) with space-time quadrature, FP64
+ * update, and the CFL reduction of the updated state.  SSPRK: per stage the
+ * ghost zones at the stage time, reconstruction, face values, Riemann fluxes
+ * over the face points and the FP64 stage combination; the CFL reduction of
+ * the last stage.  dt > 0: use it; dt <= 0: use the
  * device-resident dt (from awe_cfl_dt or the previous step) without any host
  * round trip.  t advances by dt.  dt_next_out (may be NULL, then no
  * synchronisation): cfg.cfl / signal-speed max of the updated state.
@@ -170,10 +176,12 @@ int awe_check(awe_grid* g);
 int awe_probe_modes(awe_grid* g, double* W);
 /* Face quadrature states of every box zone after the predictor with time step
  * dt: host buffer [dir][side][q][var][box zone], side 0 = lower face; q =
- * i_t1 + 2*(i_t2 + 2*i_time) (3D) or i_t1 + 2*i_time (2D), Gauss-Legendre
- * points with 2 nodes per transverse dimension and in time. */
+ * i_t1 + nq*(i_t2 + nq*i_time) (3D) or i_t1 + nq*i_time (2D), Gauss-Legendre
+ * points with nq = 2 nodes per transverse dimension and in time at orders 3
+ * and 4, nq = 1 (the face centre at mid-step) at order 2.  ADER grids only
+ * (AWE_ERR_STATE otherwise), like awe_probe_fluxes. */
 int awe_probe_face_states(awe_grid* g, double dt, double* FS);
-/* Face-averaged HLLC fluxes of the active faces for time step dt: host buffer,
+/* Face-averaged Riemann fluxes of the active faces for time step dt: host buffer,
  * per direction d the block [var][faces], faces (n_x + [d==0]) x (n_y +
  * [d==1]) x (n_z + [d==2]) with x fastest, blocks concatenated over d. */
 int awe_probe_fluxes(awe_grid* g, double dt, double* F);
@@ -186,7 +194,7 @@ int awe_profile(awe_grid* g, int enable);
  * since timing was enabled (synchronises). */
 int awe_profile_count(void);
 int awe_profile_read(awe_grid* g, int kind, const char** name, long* launches, double* total_ms);
-/* ---- learned troubled-zone gate (not in the paper; see DESIGN.md) ----
+/* ---- learned troubled-zone gate (not in the paper) ----
  * Features: for each direction d and for rho and E, the 2N differences
  * f(i+k+1-N) - f(i+k-N), k = 0..2N-1, divided by their largest magnitude
  * (0 for constant data), then that magnitude over |f(i)| + 1e-12, times 100,

@@ -14,7 +14,7 @@
  *
  * Readings the paper does not fix (its refs [9], [10], [12], [22], [40] are
  * not part of the text) are stated where they are used; parity is pinned by
- * the tests listed in the design doc, not by this file.
+ * the oracle tests (tests/test_oracle_*.py), not by this file.
  */
 #include "ora.h"
 

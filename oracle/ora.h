@@ -12,8 +12,9 @@
  * extends each zone's polynomial in time, and a Riemann-solver corrector whose
  * face fluxes update the zone means, followed by the CFL reduction of Fig. 7.
  * The paper names the ingredients but gives no formulas; the readings used
- * here (basis, stencils, weights, Picard predictor, HLLC, quadrature, BCs) are
- * listed one by one in the design doc and in the comments of ora.c.
+ * here (basis, stencils, weights, Picard predictor, Riemann solvers,
+ * quadrature, BCs, the Runge-Kutta variant) are stated one by one in the
+ * comments of ora.c.
  *
  * Layout of every state array: conserved variables, structure of arrays,
  * [var][z][y][x], x fastest.  "Ghosted" arrays carry g = order ghost zones on

@@ -1,7 +1,7 @@
 /*
  * ora_gate.c -- oracle of the learned troubled-zone gate (TEST INFRASTRUCTURE
  * ONLY; see ora.h).  The paper has no learned part: this follows the gate's
- * definition in the design doc.  Labels come from the method itself (deviation of
+ * definition stated below.  Labels come from the method itself (deviation of
  * the WENO nonlinear weights from the linear weights); the network is a
  * 2x32 ReLU MLP on stencil features; its decision is taken in FP32 with a fixed
  * summation order so that the CUDA path and this oracle reach identical flags.

@@ -4,7 +4,7 @@ Counted from the loop structure of the kernels (csrc/): an FMA counts 2
 flops, an add, subtract or multiply 1; divisions and square roots are
 counted apart (they are not flops of the FMA pipe).  These are the numerators
 of the ALU roofline fractions; they are checked against the executed
-FP64/FP32 instruction counts of an ncu capture.
+FP64/FP32 instruction counts of an ncu capture (profiles/).
 
 Units: the predictor and reconstruction run on the box of zones (active
 zones plus one layer per side), the flux kernel on faces, the update on
