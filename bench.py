@@ -31,6 +31,15 @@ PEAK_FP64 = SMS * 2 * 2 * CLK / 1e12      # 1.259 TFLOP/s
 PEAK_FP32 = SMS * 128 * 2 * CLK / 1e12    # 80.5 TFLOP/s
 
 
+def hbm_peak():
+    """measured copy bandwidth of the GB300s (GB/s), else the
+    profiling recipe's fallback"""
+    try:
+        return float(json.load(open(MEASURED_PEAKS))["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +366,9 @@ def run_native(args, rank, world, local):
             sc = np.abs(U1[0]).sum()
             f32["rel_l1_vs_fp64_gpu_one_step"] = max(
                 float(np.abs(U1f[v] - U1[v]).sum() / max(np.abs(U1[v]).sum(), sc)) for v in range(5))
+            sci = np.abs(U1[0]).max()
+            f32["rel_linf_vs_fp64_gpu_one_step"] = max(
+                float(np.abs(U1f[v] - U1[v]).max() / max(np.abs(U1[v]).max(), sci)) for v in range(5))
         forms["fp32_bulk"] = f32
 
     if not args.no_forms and args.form == "fp64":
@@ -374,6 +386,15 @@ def run_native(args, rank, world, local):
         cpu, parity = cpu_baseline_and_parity(prob, U1, Uh.numpy(), dt0)
 
     peak = PEAK_FP64 if args.form == "fp64" else PEAK_FP32
+    # the same kernel against the HBM roofline: its measured DRAM bytes per
+    # launch (ncu, profiles/traffic.json) over its CUDA-event launch time
+    hpk, hsrc = hbm_peak()
+    hbm_line = None
+    if traffic is not None and args.form == "fp64":
+        gbs = traffic / (avg_pred * 1e-3) / 1e9
+        hbm_line = {"achieved_gbs": gbs, "peak_gbs": hpk, "frac": gbs / hpk, "peak_source": hsrc,
+                    "step_state_bytes": 2 * nbytes,
+                    "note": "FP64-pipe bound: DRAM traffic is a small fraction of the HBM roofline"}
     if rank == 0:
         line = {
             "metric": "zone-updates/sec per full ADER-WENO step at stated L1 error vs FP64 oracle",
@@ -396,7 +417,8 @@ def run_native(args, rank, world, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"predictor (k_predict_fact<{'double' if args.form == 'fp64' else 'float'}>)",
                          "peak_source": f"derived: 152 SMs x {'2 FP64' if args.form == 'fp64' else '128 FP32'} FMA/clk x 2 x 2.07 GHz",
-                         "algorithmic_flops_per_launch": flops_pred, "avg_launch_ms": avg_pred},
+                         "algorithmic_flops_per_launch": flops_pred, "avg_launch_ms": avg_pred,
+                         "hbm": hbm_line},
             "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
             "clocks": clocks,
             "e2e": {"value": world * zones * e2e_steps / (e2e_ms * 1e-3), "unit": "zone-updates/s",

@@ -51,21 +51,48 @@ bool rk_scheme(int stages, RKScheme& r) {
 // ---------------------------------------------------------------------------
 // face states of the reconstructed polynomial (no time evolution)
 // ---------------------------------------------------------------------------
-// FS[d][side][p][var][box zone], p < NP (face points only); fw the spatial
-// mode values at the ADER face points, whose first NP rows per (d, side) are
-// the time-independent face points.  With the positivity fallback a zone with
-// a non-physical face state uses its zone mean at every face point.
+// FS[d][side][p][var][box zone], p = i1 + nq*i2 < NP (face points only, the
+// ADER face point order at the first time point).  Factorised per direction
+// d: the normal axis at +-1/2 first, split into the even and odd Legendre
+// terms (P_a(-1/2) = (-1)^a P_a(1/2)), which gives both sides at once; then
+// the transverse axes at their Gauss nodes +-g, again by parity.  With the
+// positivity fallback a zone with a non-physical face state uses its zone mean
+// at every face point.
+template <typename T> struct FaceConsts {
+  T ph[4];  // P_a(1/2)
+  T pg[4];  // P_p at the upper transverse Gauss node (0 with one node)
+};
+
+// index of the spatial mode with exponents (e0, e1, e2) (c outermost, a innermost)
+template <int D, int N>
+__host__ __device__ constexpr int mode_index(int e0, int e1, int e2) {
+  int idx = 0;
+  if (D == 3)
+    for (int c = 0; c < e2; ++c) idx += (N - c + 1) * (N - c + 2) / 2;
+  const int M = D == 3 ? N - e2 : N;
+  for (int b = 0; b < e1; ++b) idx += M - b + 1;
+  return idx + e0;
+}
+// mode of normal exponent an and transverse exponents (p1, p2) for direction d
+// (t1 < t2 the transverse dimensions)
+template <int D, int N>
+__host__ __device__ constexpr int face_mode(int d, int an, int p1, int p2) {
+  return D == 2 ? (d == 0 ? mode_index<D, N>(an, p1, 0) : mode_index<D, N>(p1, an, 0))
+                : (d == 0 ? mode_index<D, N>(an, p1, p2)
+                          : d == 1 ? mode_index<D, N>(p1, an, p2) : mode_index<D, N>(p1, p2, an));
+}
+// transverse exponent pairs (p1, p2), p1 + p2 <= N, p2 outermost (3D), or p1 (2D)
+template <int N> __host__ __device__ constexpr int pair_index(int p1, int p2) {
+  return p2 * (N + 1) - p2 * (p2 - 1) / 2 + p1;
+}
+
 template <int D, int N, typename T>
 __global__ void __launch_bounds__(128) k_face_eval(Geo q, Region box, const T* __restrict__ W,
-                                                   const T* __restrict__ fw, T* __restrict__ FS) {
-  constexpr int NV = D + 2, NS = Modes<D, N>::NS, NFQ = Modes<D, N>::NFQ;
-  constexpr int NP = kPoints<D, N, true>(), NR = D * 2 * NP;
-  __shared__ T sfw[NR * NS];
-  for (int i = threadIdx.x; i < NR * NS; i += blockDim.x) {
-    int m = i % NS, row = i / NS, p = row % NP, ds = row / NP;
-    sfw[i] = fw[((long long)ds * NFQ + p) * NS + m];
-  }
-  __syncthreads();
+                                                   FaceConsts<T> fc, T* __restrict__ FS) {
+  constexpr int NV = D + 2, NS = Modes<D, N>::NS, NQ = Modes<D, N>::NQ;
+  constexpr int NP = kPoints<D, N, true>();
+  constexpr int NPAIR = D == 3 ? (N + 1) * (N + 2) / 2 : N + 1;
+  constexpr int P2MAX = D == 3 ? N : 0;
   const long long nb = box.size();
   const T gm1 = (T)(q.gamma - 1.0);
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nb;
@@ -75,15 +102,73 @@ __global__ void __launch_bounds__(128) k_face_eval(Geo q, Region box, const T* _
       T w[NS];
 #pragma unroll
       for (int m = 0; m < NS; ++m) w[m] = W[((long long)v * NS + m) * nb + r];
-#pragma unroll 2
-      for (int row = 0; row < NR; ++row) {
-        T acc = T(0);
 #pragma unroll
-        for (int m = 0; m < NS; ++m) acc = fma(w[m], sfw[row * NS + m], acc);
-        FS[((long long)row * NV + v) * nb + r] = acc;
+      for (int d = 0; d < D; ++d) {
+        // normal axis: even and odd parts for every transverse pair
+        T E[NPAIR], O[NPAIR];
+#pragma unroll
+        for (int p2 = 0; p2 <= P2MAX; ++p2)
+#pragma unroll
+          for (int p1 = 0; p1 <= N - p2; ++p1) {
+            T e = T(0), o = T(0);
+#pragma unroll
+            for (int an = 0; an <= N - p1 - p2; ++an) {
+              const T x = w[face_mode<D, N>(d, an, p1, p2)];
+              if (an & 1) o = fma(x, fc.ph[an], o);
+              else e = an == 0 ? x : fma(x, fc.ph[an], e);
+            }
+            E[pair_index<N>(p1, p2)] = e;
+            O[pair_index<N>(p1, p2)] = o;
+          }
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          // transverse axis t1: V[i1][p2]
+          T V[NQ][P2MAX + 1];
+#pragma unroll
+          for (int p2 = 0; p2 <= P2MAX; ++p2) {
+            T ev = T(0), od = T(0);
+#pragma unroll
+            for (int p1 = 0; p1 <= N - p2; ++p1) {
+              const int k = pair_index<N>(p1, p2);
+              const T wt = side ? E[k] + O[k] : E[k] - O[k];
+              if (p1 & 1) od = fma(wt, fc.pg[p1], od);
+              else ev = p1 == 0 ? wt : fma(wt, fc.pg[p1], ev);
+            }
+            if (NQ == 2) {
+              V[0][p2] = ev - od;
+              V[NQ - 1][p2] = ev + od;
+            } else {
+              V[0][p2] = ev;  // at the centre the odd terms vanish
+            }
+          }
+          const long long row0 = (long long)(d * 2 + side) * NP;
+          if (D == 2) {
+#pragma unroll
+            for (int i1 = 0; i1 < NQ; ++i1)
+              FS[((row0 + i1) * NV + v) * nb + r] = V[i1][0];
+          } else {
+            // transverse axis t2
+#pragma unroll
+            for (int i1 = 0; i1 < NQ; ++i1) {
+              T ev = T(0), od = T(0);
+#pragma unroll
+              for (int p2 = 0; p2 <= P2MAX; ++p2) {
+                if (p2 & 1) od = fma(V[i1][p2], fc.pg[p2], od);
+                else ev = p2 == 0 ? V[i1][p2] : fma(V[i1][p2], fc.pg[p2], ev);
+              }
+              if (NQ == 2) {
+                FS[((row0 + i1 + NQ * 0) * NV + v) * nb + r] = ev - od;
+                FS[((row0 + i1 + NQ * 1) * NV + v) * nb + r] = ev + od;
+              } else {
+                FS[((row0 + i1) * NV + v) * nb + r] = ev;
+              }
+            }
+          }
+        }
       }
     }
     if (q.fallback) {
+      constexpr int NR = D * 2 * NP;
       bool bad = false;
       for (int row = 0; row < NR; ++row) {
         T u[NV];
@@ -102,18 +187,32 @@ __global__ void __launch_bounds__(128) k_face_eval(Geo q, Region box, const T* _
   }
 }
 
+template <typename T> static FaceConsts<T> face_consts(int N) {
+  FaceConsts<T> c;
+  const int nq = (N + 2) / 2;
+  double x[4], w[4];
+  gauss_nodes(nq, x, w);
+  for (int a = 0; a < 4; ++a) {
+    c.ph[a] = (T)basisP(a, 0.5);
+    c.pg[a] = (T)basisP(a, x[nq - 1]);
+  }
+  return c;
+}
+
 void launch_face_eval(const Geo& q, int prec, const void* W, int z0, int z1, const void* tab,
                       const PTabLayout& L, void* FS, cudaStream_t s) {
+  (void)tab;
+  (void)L;
   Region box = region_box(q, z0, z1);
   int blocks = grid_for(box.size(), 128, 152LL * 16);
 #define AWE_FACE(D_, N_)                                                                   \
   if (q.dim == D_ && q.N == N_) {                                                          \
     if (prec == AWE_FP64)                                                                  \
       k_face_eval<D_, N_, double><<<blocks, 128, 0, s>>>(                                  \
-          q, box, (const double*)W, (const double*)tab + L.fw, (double*)FS);               \
+          q, box, (const double*)W, face_consts<double>(N_), (double*)FS);                 \
     else                                                                                   \
       k_face_eval<D_, N_, float><<<blocks, 128, 0, s>>>(                                   \
-          q, box, (const float*)W, (const float*)tab + L.fw, (float*)FS);                  \
+          q, box, (const float*)W, face_consts<float>(N_), (float*)FS);                    \
   }
   AWE_FACE(2, 1) AWE_FACE(2, 2) AWE_FACE(2, 3) AWE_FACE(3, 1) AWE_FACE(3, 2) AWE_FACE(3, 3)
 #undef AWE_FACE

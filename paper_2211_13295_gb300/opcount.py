@@ -50,7 +50,11 @@ def _hllc(D):
 
 def _weno(N, linear):
     """weno1d: 2N differences (counted by the caller), candidates, beta,
-    FP64 weights (product form), combination."""
+    FP64 weights (product form), combination.  N = 1 (order 2): the MC
+    limiter of Fig. 3 (sum, three scaled magnitudes, two minima, the sign
+    factor and its product)."""
+    if N == 1:
+        return 8, 0
     # candidate stencils: number of nonzero weights per coefficient
     terms = {2: [2, 2, 2, 2, 2, 2], 3: [3, 3, 3, 3, 2, 3, 3, 2, 3, 3, 3, 3]}[N]
     cand = sum(1 + 2 * (t - 1) for t in terms)
