@@ -257,6 +257,44 @@ def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
     return out
 
 
+def small_grid_graph():
+    """The 2D workload (isentropic vortex, 64^2, order 3, CFL 0.4): a grid
+    small enough that kernel launches dominate a step.  Per-step time of 100
+    steps launched one by one, and of the same 100 steps replayed from one
+    CUDA graph (awe.StepGraph), CUDA events on the grid's stream."""
+    import torch
+    from paper_2211_13295_gb300 import awe
+    from paper_2211_13295_gb300 import problems as P
+    prob = P.vortex2d(n=64, order=3)
+    K = 100
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = awe.Grid(prob)
+        g.set_state(prob.initial_state())
+        g.cfl_dt()
+        g.step(0.0, sync=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(K):
+            g.step(0.0, sync=False)
+        e1.record(s)
+        s.synchronize()
+        eager = e0.elapsed_time(e1) / K
+        sg = awe.StepGraph(g, K, s)
+        sg.replay()
+        s.synchronize()
+        e0.record(s)
+        sg.replay()
+        e1.record(s)
+        s.synchronize()
+        graph = e0.elapsed_time(e1) / K
+        g.check()
+        g.close()
+    return {"workload": "vortex2d 64^2 order 3 HLLC CFL 0.4", "eager_ms_per_step": eager,
+            "graph_ms_per_step": graph, "graph_zone_updates_per_s": prob.zones / (graph * 1e-3),
+            "eager_zone_updates_per_s": prob.zones / (eager * 1e-3)}
+
+
 def gated_forms(args, prob, Uh, U1, zones, world):
     """Train the troubled-zone gate on the GPU (labels from the method on
     short seeded runs of the vortex, Sod, blast and Kelvin-Helmholtz
@@ -374,8 +412,9 @@ def run_native(args, rank, world, local):
     if not args.no_forms and args.form == "fp64":
         forms.update(gated_forms(args, prob, Uh, U1, zones, world))
 
-    table2 = table4 = solvers = None
+    table2 = table4 = solvers = small = None
     if not args.no_forms and args.form == "fp64":
+        small = small_grid_graph()
         table2 = orders_192(args, world)
         table4 = orders_192(args, world, scheme="ssprk")
         solvers = {k: orders_192(args, world, riemann=k, orders=(4,))["O4"] for k in ("hll", "hllem", "rusanov")}
@@ -429,6 +468,7 @@ def run_native(args, rank, world, local):
             "orders_tgv192_fp64": table2,
             "ssprk_orders_tgv192_fp64": table4,
             "riemann_tgv192_o4_fp64": solvers,
+            "small_grid_cuda_graph": small,
         }
         print(json.dumps(line))
 

@@ -368,3 +368,26 @@ def __getattr__(name):
     if name.startswith("awe_"):
         return getattr(lib(), name)
     raise AttributeError(name)
+
+
+class StepGraph:
+    """`steps` steps of a grid with the device-resident time step, captured
+    into one CUDA graph: replay() launches all their kernels with one call
+    (for small grids, where a step is a few microseconds of work per kernel
+    and launch overhead dominates).  The grid must live on `stream` (create it
+    inside `with torch.cuda.stream(stream)`) and have stepped once eagerly, so
+    that every kernel is loaded before the capture; awe_step makes no
+    allocation and no host synchronisation when no dt_next is requested."""
+
+    def __init__(self, grid, steps, stream):
+        import torch
+        if grid._stream.value != stream.cuda_stream:
+            raise ValueError("the grid was created on another stream")
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=stream):
+            for _ in range(steps):
+                grid.step(0.0, sync=False)
+        self.steps = steps
+
+    def replay(self):
+        self.graph.replay()
