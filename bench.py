@@ -257,6 +257,57 @@ def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
     return out
 
 
+def other_configs(world, gate_params):
+    """Zone-updates/s of the other workloads at their full sizes, in their
+    forms: the double Mach reflection (4096x1024, order 3, FP32 bulk, with the
+    positivity fallback), the Kelvin-Helmholtz layer (512^3, order 4, FP32
+    bulk with the trained gate, 64-plane slabs) and the blast (384^3, order 4,
+    FP64 with the trained gate and the positivity fallback, 128-plane slabs).
+    Two timed steps after one warm-up step each; the status after the timed
+    steps is reported (the blast loses positivity in a few zones on its first
+    step, in the oracle as on the GPU)."""
+    import torch
+    from paper_2211_13295_gb300 import awe
+    from paper_2211_13295_gb300 import problems as P
+    runs = [("dmr_4096x1024_o3_fp32_fallback", P.dmr(nx=4096, ny=1024).replace(fallback=True), "fp32", False, 0),
+            ("kh3d_512_o4_fp32_gate_slab64", P.kh3d(n=512, order=4), "fp32", True, 64),
+            ("blast3d_384_o4_fp64_gate_fallback_slab128", P.blast3d(n=384, order=4).replace(fallback=True),
+             "fp64", True, 128)]
+    out = {}
+    for name, prob, prec, gate, slab in runs:
+        g = awe.Grid(prob, prec=prec, gate=gate, slab=slab)
+        if gate:
+            g.gate_set_weights(gate_params)
+        g.set_state(prob.initial_state())
+        g.cfl_dt()
+        g.step(0.0, sync=False)
+        torch.cuda.synchronize()
+        g.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            g.step(0.0, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world) / 2
+        prof = g.profile_read()
+        g.profile(False)
+        status = "ok"
+        try:
+            g.check()
+        except awe.AweError as e:
+            status = f"status {e.code}: {e}"
+        d = {"value": world * prob.zones / (ms * 1e-3), "unit": "zone-updates/s", "ms_per_step": ms,
+             "zones": prob.zones, "status": status,
+             "stage_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}}
+        if gate:
+            fl, tot = g.gate_stats()
+            d["flagged_fraction"] = fl / tot
+        g.close()
+        out[name] = d
+    return out
+
+
 def small_grid_graph():
     """The 2D workload (isentropic vortex, 64^2, order 3, CFL 0.4): a grid
     small enough that kernel launches dominate a step.  Per-step time of 100
@@ -333,6 +384,7 @@ def gated_forms(args, prob, Uh, U1, zones, world):
             d["rel_l1_vs_full_weno_fp64_one_step"] = max(
                 float(np.abs(Ug1[v] - U1[v]).sum() / max(np.abs(U1[v]).sum(), sc)) for v in range(5))
         out[f"{prec}_gated"] = d
+    out["_params"] = params
     out["gate_training"] = {"rows": int(X.shape[0]), "positive_fraction": float(Y.mean()),
                             "accuracy": acc, "recall": recall, "train_seconds": train_s,
                             "collect_seconds": collect_s,
@@ -411,10 +463,12 @@ def run_native(args, rank, world, local):
 
     if not args.no_forms and args.form == "fp64":
         forms.update(gated_forms(args, prob, Uh, U1, zones, world))
+        gate_params = forms.pop("_params")
 
-    table2 = table4 = solvers = small = None
+    table2 = table4 = solvers = small = others = None
     if not args.no_forms and args.form == "fp64":
         small = small_grid_graph()
+        others = other_configs(world, gate_params)
         table2 = orders_192(args, world)
         table4 = orders_192(args, world, scheme="ssprk")
         solvers = {k: orders_192(args, world, riemann=k, orders=(4,))["O4"] for k in ("hll", "hllem", "rusanov")}
@@ -469,6 +523,7 @@ def run_native(args, rank, world, local):
             "ssprk_orders_tgv192_fp64": table4,
             "riemann_tgv192_o4_fp64": solvers,
             "small_grid_cuda_graph": small,
+            "other_workloads": others,
         }
         print(json.dumps(line))
 
