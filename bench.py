@@ -451,7 +451,9 @@ def run_native(args, rank, world, local):
                "dtype": "f32 bulk, f64 update/weights/CFL",
                "predictor_ms": mp32 / max(np32, 1),
                "predictor_tflops": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12,
-               "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32}
+               "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32,
+               "predictor_bound": "shared-memory bandwidth: 70% of the LSU wavefront peak, FP32 pipe 17.5% "
+                                  "(ncu, profiles/predictor_fp32_tgv48.md)"}
         if U1f is not None:
             sc = np.abs(U1[0]).sum()
             f32["rel_l1_vs_fp64_gpu_one_step"] = max(
