@@ -262,22 +262,27 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   for (int d = 0; d < 3; ++d) {
     if constexpr ((kStatic<T> & kStP1) != 0) {
       {
-        const int n2 = lane & 15, h = lane >> 4;
+        // lanes own (n2, a group of variables: 0-2 or 3-4) and compute every
+        // (p,e) pair of a variable from its 4 x (EMAX+1) values, loaded once
+        const int n2 = lane & 15, vh = lane >> 4;
         const int a0 = n2 & 3, a1 = n2 >> 2;
         const int sbase = d < 2 ? (a0 + 4 * a1) : (a0 + 16 * a1);
         const int sstr = d < 2 ? 16 : 4;
         const T* y1 = Y1 + (d * 5) * 64 * 3;
-        // the (p,e) pairs of this half of the warp
-#pragma unroll
-        for (int pe = 0; pe < NPE; ++pe) {
-          if ((pe & 1) != h) continue;
-          const int p = pair2_p(pe), e = pair2_e(pe);
 #pragma unroll 1
-          for (int v = 0; v < 5; ++v) {
-            const T* yv = y1 + v * 64 * 3 + sbase * 3 + e;
+        for (int v = 3 * vh; v < (vh ? 5 : 3); ++v) {
+          const T* yv = y1 + v * 64 * 3 + sbase * 3;
+          T y[EMAX + 1][4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int e = 0; e <= EMAX; ++e) y[e][m] = yv[m * sstr * 3 + e];
+#pragma unroll
+          for (int pe = 0; pe < NPE; ++pe) {
+            const int p = pair2_p(pe), e = pair2_e(pe);
             T acc = T(0);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) acc = fma(yv[m * sstr * 3], tc.WPN[p][m], acc);
+            for (int m = 0; m < 4; ++m) acc = fma(y[e][m], tc.WPN[p][m], acc);
             Y2[(v * 16 + n2) * 6 + pe] = acc;
           }
         }
@@ -308,14 +313,21 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
         const int nbase = d == 0 ? n1 : 4 * n1;
         const int nstr = d == 0 ? 4 : 1;
         const T* y2 = Y2 + v * 16 * 6;
+        T y[NPE][4];  // every operand once
 #pragma unroll
-        for (int tr = 0; tr < NTR; ++tr) {
-          const int p = tri2_p(tr), qq = tri2_q(tr), e = tri2_r(tr);
-          const int pe = p2idx(qq, e);
-          T acc = T(0);
+        for (int m = 0; m < 4; ++m)
 #pragma unroll
-          for (int m = 0; m < 4; ++m) acc = fma(y2[(nbase + m * nstr) * 6 + pe], tc.WPN[p][m], acc);
-          Y3[((d * 5 + v) * 4 + n1) * 10 + tr] = acc;
+          for (int pe = 0; pe < NPE; ++pe) y[pe][m] = y2[(nbase + m * nstr) * 6 + pe];
+#pragma unroll
+        for (int pe = 0; pe < NPE; ++pe) {
+          const int qq = pair2_p(pe), e = pair2_e(pe);
+#pragma unroll
+          for (int p = 0; p <= 2 - qq - e; ++p) {
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc = fma(y[pe][m], tc.WPN[p][m], acc);
+            Y3[((d * 5 + v) * 4 + n1) * 10 + tri2idx(p, qq, e)] = acc;
+          }
         }
       }
     } else {
