@@ -165,6 +165,11 @@ int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out);
 int awe_step(awe_grid* g, double dt, double* dt_next_out);
 /* Synchronise and report a non-physical state flagged by earlier steps. */
 int awe_check(awe_grid* g);
+/* Number of box zones (active zones and one layer around them, per
+ * reconstruction: once per step for ADER, once per stage for SSPRK) whose
+ * face states went to the positivity fallback (cfg.fallback) since the last
+ * call; resets the count and synchronises.  Not in the paper. */
+int awe_fallback_count(awe_grid* g, long long* zones);
 
 /* ---- per-stage probes (same kernels as awe_step, for row-by-row parity) ----
  * The box is the active zones plus one layer on each side, [-1, n_d] in each

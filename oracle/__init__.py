@@ -306,6 +306,14 @@ class Oracle:
         lib().ora_face_states(C.byref(self.cfg), _dp(Ug), _up(flags), float(dt), _dp(FS))
         return FS
 
+    def fallback_count(self, U, t, dt, flags=None):
+        """box zones whose face states go to the positivity fallback"""
+        Ug = self.ghosted(U, t)
+        B = self.box_shape()
+        nq = ((self.prob.order + 1) // 2) ** self.dim
+        FS = np.zeros((self.dim, 2, nq, self.nv, B[2], B[1], B[0]))
+        return lib().ora_face_states(C.byref(self.cfg), _dp(Ug), _up(flags), float(dt), _dp(FS))
+
     def fluxes(self, U, t, dt, flags=None):
         """List over directions of [nv][Ez][Ey][Ex] face-averaged fluxes."""
         Ug = self.ghosted(U, t)

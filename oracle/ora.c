@@ -852,7 +852,8 @@ int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* fla
   ora_reconstruct(c, Ug, flags, W);
   double xq[NQMAX], wq[NQMAX];
   ora_gauss_legendre(NQ, xq, wq);
-#pragma omp parallel for schedule(static)
+  long nfallback = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nfallback)
   for (long bz = 0; bz < (long)nbox; ++bz) {
     double w[MAXV * MAXM], st[MAXV * MAXST];
     for (int v = 0; v < nv; ++v)
@@ -885,6 +886,7 @@ int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* fla
      * state of non-positive density or pressure (or a non-finite one) falls
      * back to first order: all its face states become the zone mean. */
     if (c->fallback && bad) {
+      nfallback += 1;
       for (int d = 0; d < dim; ++d)
         for (int side = 0; side < 2; ++side)
           for (int p = 0; p < nfq; ++p)
@@ -893,7 +895,7 @@ int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* fla
     }
   }
   free(W);
-  return 0;
+  return (int)nfallback;
 }
 
 /* Face-averaged Riemann fluxes of the active faces (Make_Flux_X/Y/Z, Fig. 5):

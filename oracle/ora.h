@@ -76,7 +76,8 @@ int ora_fill_ghosts(const ora_cfg* c, double* Ug, double t);
 int ora_reconstruct(const ora_cfg* c, const double* Ug, const unsigned char* flags, double* W);
 /* Predictor of one zone: w[var][mode] -> space-time coefficients st[var][st-mode]. */
 void ora_predict_zone(const ora_cfg* c, const double* w, double dt, double* st);
-/* Face quadrature states of every box zone: FS[dir][side][q][var][box zone]. */
+/* Face quadrature states of every box zone: FS[dir][side][q][var][box zone];
+ * returns the number of box zones sent to the positivity fallback. */
 int ora_face_states(const ora_cfg* c, const double* Ug, const unsigned char* flags,
                     double dt, double* FS);
 /* One full step on a ghost-filled state. Uout: active zones [var][z][y][x].

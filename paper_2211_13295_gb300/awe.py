@@ -69,6 +69,7 @@ def lib():
         "awe_cfl_dt": (C.c_int, [vp, C.c_double, dp]),
         "awe_step": (C.c_int, [vp, C.c_double, dp]),
         "awe_check": (C.c_int, [vp]),
+        "awe_fallback_count": (C.c_int, [vp, C.POINTER(C.c_longlong)]),
         "awe_probe_modes": (C.c_int, [vp, vp]),
         "awe_probe_face_states": (C.c_int, [vp, C.c_double, vp]),
         "awe_probe_fluxes": (C.c_int, [vp, C.c_double, vp]),
@@ -105,7 +106,7 @@ def exported_symbols():
         "awe_probe_fluxes", "awe_profile", "awe_profile_count", "awe_profile_read", "awe_gate_dims",
         "awe_gate_set_weights", "awe_gate_features", "awe_gate_labels", "awe_gate_flags", "awe_gate_stats",
         "awe_mlp_train", "awe_mlp_loss_grad", "awe_mlp_forward", "awe_measure_fma_peaks",
-        "awe_cfl_dt_noalloc",
+        "awe_cfl_dt_noalloc", "awe_fallback_count",
     ]
 
 
@@ -236,6 +237,12 @@ class Grid:
 
     def check(self):
         _check(lib().awe_check(self.h), self.h)
+
+    def fallback_count(self):
+        """box zones sent to the positivity fallback since the last call"""
+        n = C.c_longlong()
+        _check(lib().awe_fallback_count(self.h, C.byref(n)), self.h)
+        return n.value
 
     # probes --------------------------------------------------------------
     def probe_modes(self):

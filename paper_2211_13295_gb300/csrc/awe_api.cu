@@ -60,11 +60,14 @@ struct awe_grid {
   int cur = 0;
   double* d_scal = nullptr;  // [0] t, [1] dt, [2] saved dt
   unsigned long long* d_smax = nullptr;
+  unsigned long long* d_fb = nullptr;  // zones sent to the positivity fallback
   int* d_err = nullptr;
   void *X = nullptr, *Y = nullptr, *XY = nullptr, *W = nullptr, *FS = nullptr, *F = nullptr;
   double* stage = nullptr;  // state staging [nv][nact]
   double* Urk[2] = {nullptr, nullptr};  // Runge-Kutta stage states (ghosted)
   awe::RKScheme rk;
+  bool poison = false;  // AWE_POISON=1 at create: NaN-fill the intermediates before use
+  long long szX = 0, szY = 0, szXY = 0, szW = 0, szFS = 0, szF = 0;
   void* ptab = nullptr;
   PTabLayout L;
   size_t bytesT = 8;
@@ -206,9 +209,25 @@ Sizes buffer_sizes(const Geo& q, int slab) {
   return s;
 }
 
+// Debug aid (AWE_POISON=1 at awe_create): every intermediate buffer is filled
+// with NaN bit patterns before each slab's pipeline, so that a kernel reading
+// an element that no earlier stage of the same slab wrote makes the result
+// differ (tests compare poisoned and plain steps bit for bit).
+void poison_slab_buffers(awe_grid* g) {
+  if (!g->poison) return;
+  const size_t b = g->bytesT;
+  cudaMemsetAsync(g->X, 0xFF, b * g->szX, g->s);
+  cudaMemsetAsync(g->Y, 0xFF, b * g->szY, g->s);
+  cudaMemsetAsync(g->XY, 0xFF, b * g->szXY, g->s);
+  cudaMemsetAsync(g->W, 0xFF, b * g->szW, g->s);
+  cudaMemsetAsync(g->FS, 0xFF, b * g->szFS, g->s);
+  cudaMemsetAsync(g->F, 0xFF, b * g->szF, g->s);
+}
+
 // the pipeline of one slab: recon, predictor, flux, (update)
 void run_slab(awe_grid* g, int z0, int z1, bool do_flux, bool do_update, const unsigned char* flags) {
   const Geo& q = g->q;
+  poison_slab_buffers(g);
   int m0 = prof_mark(g);
   cudaEvent_t evs[3];
   cudaEvent_t* ev = nullptr;
@@ -260,6 +279,7 @@ const unsigned char* gate_flags_for_step(awe_grid* g, const double* U = nullptr)
 void run_slab_rk(awe_grid* g, const double* in, int z0, int z1, const unsigned char* flags,
                  const RKOut& o1, const RKOut& o2, int nout, bool last) {
   const Geo& q = g->q;
+  poison_slab_buffers(g);
   int m0 = prof_mark(g);
   cudaEvent_t evs[3];
   cudaEvent_t* ev = nullptr;
@@ -454,6 +474,11 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
     return rc;
   }
   Sizes sz = buffer_sizes(q, q.dim == 3 ? g->slab : 1);
+  g->szX = sz.X, g->szY = sz.Y, g->szXY = sz.XY, g->szW = sz.W, g->szFS = sz.FS, g->szF = sz.F;
+  {
+    const char* pz = std::getenv("AWE_POISON");
+    g->poison = pz && pz[0] == '1';
+  }
   size_t nbytesU = sizeof(double) * q.nv * q.ntot;
   struct A { void** p; size_t n; const char* what; };
   std::vector<A> allocs = {
@@ -462,6 +487,7 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
       {(void**)&g->d_scal, 4 * sizeof(double), "scalars"},
       {(void**)&g->d_smax, sizeof(unsigned long long), "smax"},
       {(void**)&g->d_err, sizeof(int), "err"},
+      {(void**)&g->d_fb, sizeof(unsigned long long), "fallback counter"},
       {&g->X, g->bytesT * sz.X, "recon X fields"},
       {&g->Y, g->bytesT * sz.Y, "recon Y fields"},
       {&g->XY, g->bytesT * sz.XY, "recon XY fields"},
@@ -504,6 +530,8 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_scal, 0, 4 * sizeof(double), g->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_smax, 0, sizeof(unsigned long long), g->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_fb, 0, sizeof(unsigned long long), g->s);
+  g->q.fb_count = g->d_fb;
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
   if (e != cudaSuccess) {
     g_create_error = std::string("initialisation: ") + cudaGetErrorString(e);
@@ -523,8 +551,9 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
 int awe_destroy(awe_grid* g) {
   if (!g) return AWE_OK;
   cudaStreamSynchronize(g->s);
-  void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax, g->d_err, g->X,     g->Y,     g->XY,
-                  g->W,    g->FS,   g->F,      g->stage,  g->ptab,  g->Urk[0], g->Urk[1]};
+  void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax,  g->d_err,  g->X,    g->Y,
+                  g->XY,   g->W,    g->FS,     g->F,      g->stage,  g->ptab, g->Urk[0],
+                  g->Urk[1], g->d_fb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   awe::gate_free(g->gate);
@@ -598,6 +627,12 @@ int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out) {
 int awe_step(awe_grid* g, double dt, double* dt_next_out) {
   if (!g) return AWE_ERR_ARG;
   if (g->cfg.gate && !g->gate.have_weights) return fail(g, AWE_ERR_STATE, "gate enabled without weights");
+  if (g->poison) {
+    const size_t nbytesU = sizeof(double) * g->q.nv * g->q.ntot;
+    cudaMemsetAsync(g->U[1 - g->cur], 0xFF, nbytesU, g->s);
+    for (int b = 0; b < 2; ++b)
+      if (g->Urk[b]) cudaMemsetAsync(g->Urk[b], 0xFF, nbytesU, g->s);
+  }
   if (dt > 0) launch_set_scalar(g->d_scal + 1, dt, g->s);
   if (g->cfg.scheme == AWE_SCHEME_SSPRK) {
     int rc = rk_step(g);
@@ -618,6 +653,16 @@ int awe_step(awe_grid* g, double dt, double* dt_next_out) {
     CK(g, cudaMemcpyAsync(dt_next_out, g->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, g->s));
     return awe_check(g);
   }
+  return AWE_OK;
+}
+
+int awe_fallback_count(awe_grid* g, long long* zones) {
+  if (!g || !zones) return fail(g, AWE_ERR_ARG, "null argument");
+  unsigned long long n = 0;
+  CK(g, cudaMemcpyAsync(&n, g->d_fb, sizeof(n), cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaMemsetAsync(g->d_fb, 0, sizeof(n), g->s));
+  CK(g, cudaStreamSynchronize(g->s));
+  *zones = (long long)n;
   return AWE_OK;
 }
 

@@ -31,6 +31,7 @@ struct Geo {
   double pre[5];
   int fallback;  // positivity fallback of the face states
   int riemann;   // awe_riemann: Riemann solver of the corrector
+  unsigned long long* fb_count;  // device counter of zones sent to the fallback (may be null)
 };
 
 // index of an active-relative coordinate in a ghosted array

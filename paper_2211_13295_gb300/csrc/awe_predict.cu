@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
         }
         bad = bad || !state_physical<D, T>(u, gm1);
       }
+      if (bad && q.fb_count) atomicAdd(q.fb_count, 1ULL);
     }
     for (int row = 0; row < D * 2 * NFQ; ++row) {
       const T* fw = FW + (long long)row * NS;
@@ -732,6 +733,7 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
     if (q.fallback)
       for (int row = lane; row < 48; row += 32) bad = bad || !state_physical5<T>(fv + row * 5, gm1);
     bad = __any_sync(0xffffffffu, bad) && q.fallback;
+    if (bad && lane == 0 && q.fb_count) atomicAdd(q.fb_count, 1ULL);
     __syncwarp();
     for (int it = lane; it < 240; it += 32) {
       int v = it % 5, row = it / 5;

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(128) k_face_eval(Geo q, Region box, const T* _
         bad = bad || !state_physical<D, T>(u, gm1);
       }
       if (bad) {
+        if (q.fb_count) atomicAdd(q.fb_count, 1ULL);
 #pragma unroll 1
         for (int v = 0; v < NV; ++v) {
           const T mean = W[((long long)v * NS) * nb + r];

@@ -354,3 +354,24 @@ def test_order2_vortex_run_matches_the_oracle(awe):
     Ug = g.get_state()
     for v in range(prob.nv):
         assert rel_l1(Ug[v], U[v]) <= 1e-12 * 30, v
+
+
+@pytest.mark.parametrize("name", ["dmr", "blast"])
+def test_fallback_count_matches_the_oracle(awe, name):
+    """The number of box zones whose face states go to the positivity
+    fallback in one step equals the oracle's (an integer decision taken in
+    FP64 on both sides)."""
+    if name == "dmr":
+        prob = P.dmr(nx=96, ny=24, order=3).replace(fallback=True)
+    else:
+        prob = P.blast3d(n=24, order=4).replace(fallback=True)
+    U = prob.initial_state()
+    orc = oracle.Oracle(prob)
+    dt = orc.cfl_dt(U, prob.cfl)
+    g = awe.Grid(prob)
+    g.set_state(U)
+    g.step(dt, sync=False)
+    n_gpu = g.fallback_count()
+    g.close()
+    n_orc = orc.fallback_count(U, 0.0, dt)
+    assert n_gpu == n_orc and n_orc > 0, (n_gpu, n_orc)
