@@ -252,8 +252,8 @@ def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
         ms = max_over_ranks(ms, world)
         g.close()
         out[f"O{order}"] = world * prob.zones * 3 / (ms * 1e-3)
-        if scheme != "ader" and order == 4:
-            out["O4_stage_ms_per_step"] = {k: v[1] / 3 for k, v in prof.items() if v[0]}
+        if len(orders) > 1:
+            out[f"O{order}_stage_ms_per_step"] = {k: round(v[1] / 3, 3) for k, v in prof.items() if v[0]}
     return out
 
 
