@@ -179,9 +179,9 @@ template <typename T> struct FactSmem {
   static constexpr int W = 0;                  // w[5][20]
   static constexpr int WN = W + 100;           // wn[5][64]
   static constexpr int G = WN + 320;           // g[5][15]
-  static constexpr int R1 = G + 75;            // T1/T2, C, Y2 of one direction + Y3, face values (max 1080)
+  static constexpr int R1 = sizeof(T) == 4 ? G + 76 : G + 75;   // (FP32: 16-byte aligned C rows)
   static constexpr int R2 = R1 + 1080;         // A/B, Y1 (2880)
-  static constexpr int SIZE = R2 + 2880;       // 4455
+  static constexpr int SIZE = R2 + 2880;       // 4455 (FP64), 4456 (FP32)
 };
 
 // index tables copied to shared memory once per block (lane-divergent reads
@@ -598,6 +598,57 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
       // nodes: q = wn - sum_c C P_c(z_k); fluxes; time contraction into Y1
       // (the time weights have compile-time indices: constant-bank operands)
       const Tabs<T>& tc = tabs<T>(3);
+      if constexpr (sizeof(T) == 4) {
+        // FP32: each C row (the 4 time points of one (v, i, j, c)) as one
+        // 16-byte shared-memory load
+        for (int s = lane; s < 64; s += 32) {
+          const int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
+          T pnk[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) pnk[c] = tb.PN[c][k];
+          float4 cv[5][3];
+#pragma unroll
+          for (int v = 0; v < 5; ++v)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              cv[v][c] = *reinterpret_cast<const float4*>(C + (((v * 4 + i) * 4 + j) * 3 + c) * 4);
+          T acc[3][5][3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) acc[d][v][e] = T(0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            T qn[5], F[3][5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              T x = swn[v * 64 + s];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const float4 q4 = cv[v][c];
+                const T cc = t == 0 ? q4.x : t == 1 ? q4.y : t == 2 ? q4.z : q4.w;
+                x = fma(-cc, pnk[c], x);
+              }
+              qn[v] = x;
+            }
+            phys_fluxes<3, T>(qn, gm1, F);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+              for (int v = 0; v < 5; ++v)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) acc[d][v][e] = fma(tc.WLT[e][t], F[d][v], acc[d][v][e]);
+          }
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) Y1[((d * 5 + v) * 64 + s) * 3 + e] = acc[d][v][e];
+        }
+      } else
       for (int s = lane; s < 64; s += 32) {
         int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
         T pnk[3];
