@@ -236,7 +236,7 @@ def cpu_baseline_and_parity(prob, grid_state_after, U0, dt0, n_windows=3, m=4, s
     return base, parity
 
 
-def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
+def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4), gate=None):
     """Zone-updates/s of the FP64 form at orders 2, 3 and 4 on a 192^3
     Taylor-Green grid: the grid of the paper's Tables II and IV (whose A100
     numbers were measured on an unnamed problem; context only).  scheme
@@ -246,7 +246,9 @@ def orders_192(args, world, scheme="ader", riemann="hllc", orders=(2, 3, 4)):
     out = {}
     for order in orders:
         prob = P.tgv3d(n=192, order=order, cfl=0.3).replace(scheme=scheme, riemann=riemann)
-        g = awe.Grid(prob)
+        g = awe.Grid(prob, gate=gate is not None)
+        if gate is not None:
+            g.gate_set_weights(gate)
         g.set_state(prob.initial_state())
         ms, prof = time_steps(g, 3, 3, world)
         ms = max_over_ranks(ms, world)
@@ -474,6 +476,8 @@ def run_native(args, rank, world, local):
         table2 = orders_192(args, world)
         table4 = orders_192(args, world, scheme="ssprk")
         solvers = {k: orders_192(args, world, riemann=k, orders=(4,))["O4"] for k in ("hll", "hllem", "rusanov")}
+        rk_gated = orders_192(args, world, scheme="ssprk", orders=(4,), gate=gate_params)["O4"]
+        table4["O4_gated"] = rk_gated
 
     cpu = None
     parity = None

@@ -451,6 +451,31 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   for (int v = 0; v < 5; ++v) q.pre[v] = c.pre[v];
   q.fallback = c.fallback ? 1 : 0;
   q.riemann = c.riemann;
+  // the linear-weight reconstruction folded into one stencil per mode: the
+  // candidates evaluated on unit differences, combined with the linear weights
+  memset(q.lst, 0, sizeof(q.lst));
+  memset(q.lstf, 0, sizeof(q.lstf));
+  if (q.N >= 2) {
+    for (int j = 0; j <= 2 * q.N; ++j) {
+      double d[7] = {0, 0, 0, 0, 0, 0, 0};
+      d[j] = 1.0;
+      double cf[4][3] = {{0}};
+      if (q.N == 2) {
+        double c2[3][2];
+        awe::weno_candidates_n2<double>(d, c2);
+        for (int k = 0; k < 3; ++k)
+          for (int a = 0; a < 2; ++a) cf[k][a] = c2[k][a];
+      } else {
+        awe::weno_candidates_n3<double>(d, cf);
+      }
+      for (int a = 0; a < q.N; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k <= q.N; ++k) acc += c.lin[k] * cf[k][a];
+        q.lst[a][j] = acc;
+        q.lstf[a][j] = (float)acc;
+      }
+    }
+  }
   if (c.scheme == AWE_SCHEME_SSPRK) {
     int st = c.rk_stages ? c.rk_stages : (c.order == 2 ? 2 : c.order == 3 ? 3 : 5);
     RKPlan plan;

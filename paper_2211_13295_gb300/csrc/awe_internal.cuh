@@ -32,6 +32,10 @@ struct Geo {
   int fallback;  // positivity fallback of the face states
   int riemann;   // awe_riemann: Riemann solver of the corrector
   unsigned long long* fb_count;  // device counter of zones sent to the fallback (may be null)
+  // the linear-weight reconstruction folded into one stencil per mode:
+  // lst[a][j] = sum_k lin[k] c_k[a][j] on the differences d[j] (j = 0..2N)
+  double lst[3][7];
+  float lstf[3][7];
 };
 
 // index of an active-relative coordinate in a ghosted array
@@ -403,6 +407,20 @@ __device__ __forceinline__ void weno_weights(const double* beta, const double* l
 }
 
 // Full 1D WENO: modal coefficients out[0..N-1] of modes 1..N.
+// The linear-weight reconstruction as one folded stencil per mode (2N terms):
+// the same linear combination of the candidates, in a single pass.
+template <int N, typename T>
+__device__ __forceinline__ void linear1d(const T* d, const T (*lst)[7], T* out) {
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j <= 2 * N; ++j)
+      if (j != N) acc = fma(lst[a][j], d[j], acc);
+    out[a] = acc;
+  }
+}
+
 template <int N, typename T>
 __device__ __forceinline__ void weno1d(const T* d, const double* lin, double eps, bool linear,
                                        T* out) {

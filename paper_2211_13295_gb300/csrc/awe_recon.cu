@@ -49,12 +49,14 @@ template <int N> __host__ __device__ constexpr int nxy() { return N * (N - 1) / 
 
 // one 1D reconstruction: WENO at orders 3 and 4, the MC limiter at order 2
 template <int N, typename T>
-__device__ __forceinline__ void recon1d(const T* d, const double* lin, double eps, bool linear, int v,
-                                        T* out) {
+__device__ __forceinline__ void recon1d(const T* d, const Geo& q, bool linear, int v, T* out) {
   if constexpr (N == 1) {
     out[0] = mc_slope<T>(d[2], -d[0], v == 0 ? T(2.0) : T(1.5));
+  } else if (linear) {
+    if constexpr (sizeof(T) == 8) linear1d<N, T>(d, q.lst, out);
+    else linear1d<N, T>(d, q.lstf, out);
   } else {
-    weno1d<N, T>(d, lin, eps, linear, out);
+    weno1d<N, T>(d, q.lin, q.eps, false, out);
   }
 }
 template <int N> __host__ __device__ constexpr int xy_index(int a, int b) {
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(128) k_recon_x(Geo q, Region rx, const double*
 #pragma unroll
       for (int s = -N; s <= N; ++s) d[s + N] = (T)(u[s] - u0);
       T out[N];
-      recon1d<N, T>(d, q.lin, q.eps, lin, v, out);
+      recon1d<N, T>(d, q, lin, v, out);
 #pragma unroll
       for (int a = 0; a < N; ++a) X[((long long)v * N + a) * nr + r] = out[a];
     }
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(128) k_recon_y(Geo q, Region rx, Region ry, Re
 #pragma unroll
       for (int s = -N; s <= N; ++s) d[s + N] = (T)(u[s * ystride] - u0);
       T out[N];
-      recon1d<N, T>(d, q.lin, q.eps, lin, v, out);
+      recon1d<N, T>(d, q, lin, v, out);
       if (!last) {
 #pragma unroll
         for (int bb = 0; bb < N; ++bb) Y[((long long)v * N + bb) * nr + r] = out[bb];
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(128) k_recon_y(Geo q, Region rx, Region ry, Re
 #pragma unroll
         for (int s = -N; s <= N; ++s) dx_[s + N] = xa[s * xstride] - x0;
         T o2[N];
-        recon1d<N, T>(dx_, q.lin, q.eps, lin, v, o2);
+        recon1d<N, T>(dx_, q, lin, v, o2);
 #pragma unroll
         for (int bb = 1; bb <= N - a; ++bb) {
           if (!last) XY[((long long)v * NXY + xy_index<N>(a, bb)) * nr + r] = o2[bb - 1];
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(128) k_recon_z(Geo q, Region rx, Region ry, Re
 #pragma unroll
       for (int s = -N; s <= N; ++s) d[s + N] = (T)(u[s * zstride] - u0);
       T out[N];
-      recon1d<N, T>(d, q.lin, q.eps, lin, v, out);
+      recon1d<N, T>(d, q, lin, v, out);
       Wp(v, 0, 0, 0) = (T)u0;
 #pragma unroll
       for (int c = 1; c <= N; ++c) Wp(v, 0, 0, c) = out[c - 1];
@@ -204,12 +206,12 @@ __global__ void __launch_bounds__(128) k_recon_z(Geo q, Region rx, Region ry, Re
         T dd[2 * N + 1], o2[N];
 #pragma unroll
         for (int s = -N; s <= N; ++s) dd[s + N] = xa[s * xzs] - x0;
-        recon1d<N, T>(dd, q.lin, q.eps, lin, v, o2);
+        recon1d<N, T>(dd, q, lin, v, o2);
 #pragma unroll
         for (int c = 1; c <= N - a; ++c) Wp(v, a, 0, c) = o2[c - 1];
 #pragma unroll
         for (int s = -N; s <= N; ++s) dd[s + N] = ya[s * yzs] - y0;
-        recon1d<N, T>(dd, q.lin, q.eps, lin, v, o2);
+        recon1d<N, T>(dd, q, lin, v, o2);
 #pragma unroll
         for (int c = 1; c <= N - a; ++c) Wp(v, 0, a, c) = o2[c - 1];
       }
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(128) k_recon_z(Geo q, Region rx, Region ry, Re
           T dd[2 * N + 1], o2[N];
 #pragma unroll
           for (int s = -N; s <= N; ++s) dd[s + N] = xy[s * yzs] - x0;
-          recon1d<N, T>(dd, q.lin, q.eps, lin, v, o2);
+          recon1d<N, T>(dd, q, lin, v, o2);
 #pragma unroll
           for (int c = 1; c <= N - a - bb; ++c) Wp(v, a, bb, c) = o2[c - 1];
         }

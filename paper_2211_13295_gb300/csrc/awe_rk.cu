@@ -65,7 +65,7 @@ template <typename T> struct FaceConsts {
 
 // index of the spatial mode with exponents (e0, e1, e2) (c outermost, a innermost)
 template <int D, int N>
-__host__ __device__ constexpr int mode_index(int e0, int e1, int e2) {
+__host__ __device__ constexpr int face_mode_index(int e0, int e1, int e2) {
   int idx = 0;
   if (D == 3)
     for (int c = 0; c < e2; ++c) idx += (N - c + 1) * (N - c + 2) / 2;
@@ -77,9 +77,9 @@ __host__ __device__ constexpr int mode_index(int e0, int e1, int e2) {
 // (t1 < t2 the transverse dimensions)
 template <int D, int N>
 __host__ __device__ constexpr int face_mode(int d, int an, int p1, int p2) {
-  return D == 2 ? (d == 0 ? mode_index<D, N>(an, p1, 0) : mode_index<D, N>(p1, an, 0))
-                : (d == 0 ? mode_index<D, N>(an, p1, p2)
-                          : d == 1 ? mode_index<D, N>(p1, an, p2) : mode_index<D, N>(p1, p2, an));
+  return D == 2 ? (d == 0 ? face_mode_index<D, N>(an, p1, 0) : face_mode_index<D, N>(p1, an, 0))
+                : (d == 0 ? face_mode_index<D, N>(an, p1, p2)
+                          : d == 1 ? face_mode_index<D, N>(p1, an, p2) : face_mode_index<D, N>(p1, p2, an));
 }
 // transverse exponent pairs (p1, p2), p1 + p2 <= N, p2 outermost (3D), or p1 (2D)
 template <int N> __host__ __device__ constexpr int pair_index(int p1, int p2) {

@@ -58,11 +58,12 @@ def term(v, j):
 def main():
     print("// generated by gen_stencils.py: exact rational WENO candidate stencils.")
     print("// d[j] = u(j-N) - u(0) for j = 0..2N; c[k][a] = mode a+1 of candidate k.")
-    print("// Only the nonzero weights appear, so no FMA is spent on a zero.")
+    print("// Only the nonzero weights appear, so no FMA is spent on a zero.  Host-callable")
+    print("// too: the library folds them with the linear weights into one stencil.")
     for N in (2, 3):
         S = stencils(N)
         print("template <typename T>")
-        print(f"__device__ __forceinline__ void weno_candidates_n{N}(const T* d, T c[{N + 1}][{N}]) {{")
+        print(f"__host__ __device__ __forceinline__ void weno_candidates_n{N}(const T* d, T c[{N + 1}][{N}]) {{")
         for k in range(N + 1):
             for a in range(N):
                 terms = [term(v, j) for j, v in enumerate(S[k][a]) if v != 0]
