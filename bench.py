@@ -51,6 +51,8 @@ def parse():
                     help="arithmetic form of the headline line (fp64 is the workload's)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-bulk form line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--gate", action="store_true",
+                    help="time the headline grid with the gate on (He-initialised weights; for profiling)")
     return ap.parse_args()
 
 
@@ -401,7 +403,10 @@ def run_native(args, rank, world, local):
     torch.cuda.set_device(local)
     prob = workload(args.n)
     Uh = gpu_state(prob)
-    grid = awe.Grid(prob, prec=args.form)
+    grid = awe.Grid(prob, prec=args.form, gate=args.gate)
+    if args.gate:
+        from paper_2211_13295_gb300.gate_train import he_init
+        grid.gate_set_weights(he_init(awe.gate_dims(prob.dim, prob.order)[0], 2211))
     grid.set_state(Uh.numpy())
     # one explicit step from the initial state for the stated error
     dt0 = grid.cfl_dt()

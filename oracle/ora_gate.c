@@ -73,10 +73,13 @@ int ora_weno_labels(const ora_cfg* c, const double* Ug, double tau, unsigned cha
 
 /* Features: for each direction d and for rho and E (the quantities the
  * labels look at), the 2N undivided differences delta_k = f(i+k+1-N) -
- * f(i+k-N), k = 0..2N-1, divided by their largest magnitude (the shape of the
- * stencil, which is what ratios of smoothness indicators see; 0 when the data
- * is constant), then one magnitude feature: that largest magnitude over
- * |f(i)| + 1e-12, scaled by 100 and squashed by x/(1+x).  Index
+ * f(i+k-N), k = 0..2N-1 (FP64), divided by their largest magnitude s (the
+ * shape of the stencil, which is what ratios of smoothness indicators see; 0
+ * when the data is constant), then one magnitude feature: s over |f(i)| +
+ * 1e-12, scaled by 100 and squashed by x/(1+x).  The differences and s are
+ * taken in FP64; the divisions, the scaling and the squashing in FP32 on the
+ * FP32-rounded values, each operation rounded once (a classifier input needs
+ * no more, and both implementations reach the same bits).  Index
  * (d*2 + q)*(2N+1) + k, with k = 2N the magnitude. */
 int ora_gate_features(const ora_cfg* c, const double* Ug, float* feat) {
   ggeom q;
@@ -107,9 +110,11 @@ int ora_gate_features(const ora_cfg* c, const double* Ug, float* feat) {
               sc = fmax(sc, fabs(del[t]));
             }
             float* o = f + (d * 2 + qty) * (2 * N + 1);
-            for (int t = 0; t < 2 * N; ++t) o[t] = sc > 0.0 ? (float)(del[t] / sc) : 0.0f;
-            double x = 100.0 * (sc / (fabs(vals[N]) + 1e-12));
-            o[2 * N] = (float)(x / (1.0 + x));
+            const float scf = (float)sc;
+            for (int t = 0; t < 2 * N; ++t) o[t] = scf > 0.0f ? (float)del[t] / scf : 0.0f;
+            const float den = (float)fabs(vals[N]) + 1e-12f;
+            const float x = 100.0f * (scf / den);
+            o[2 * N] = x / (1.0f + x);
           }
       }
   return 0;

@@ -82,13 +82,16 @@ def test_features_by_hand():
     # zone at active x index 7 (last left zone): the x-stencil spans 5..9; the
     # only nonzero difference is f(8) - f(7), at k = 2
     f = F[0, g + 1, g + 7]
-    # rho: differences (0, 0, -0.875, 0) -> shape (0, 0, -1, 0); magnitude 0.875/1
+    # rho: differences (0, 0, -0.875, 0) -> shape (0, 0, -1, 0); magnitude
+    # 100 * 0.875/1 squashed, in FP32 operations rounded once each
+    f32 = np.float32
     assert list(f[0:4]) == [0.0, 0.0, -1.0, 0.0]
-    assert f[4] == np.float32(87.5 / 88.5)
+    x = f32(100.0) * (f32(0.875) / (f32(1.0) + f32(1e-12)))
+    assert f[4] == x / (f32(1.0) + x)
     # E = p/(gamma-1): 2.5 | 0.25 -> shape (0, 0, -1, 0); magnitude 2.25/2.5
     assert list(f[5:9]) == [0.0, 0.0, -1.0, 0.0]
-    x = 100.0 * (2.25 / (2.5 + 1e-12))
-    assert f[9] == np.float32(x / (1 + x))
+    x = f32(100.0) * (f32(2.25) / (f32(2.5) + f32(1e-12)))
+    assert f[9] == x / (f32(1.0) + x)
     # y: constant data -> zeros
     assert np.all(f[10:] == 0)
     # zones without the full stencil get zero features
