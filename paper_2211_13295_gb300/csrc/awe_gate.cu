@@ -48,11 +48,14 @@ __device__ __forceinline__ bool zone_features(const Geo& q, const double* U, int
         del[t] = __dsub_rn(vals[t + 1], vals[t]);
         sc = fmax(sc, fabs(del[t]));
       }
+      // divisions, scaling and squashing in FP32, each rounded once
       float* o = f + (d * 2 + qty) * (2 * N + 1);
+      const float scf = __double2float_rn(sc);
 #pragma unroll
-      for (int t = 0; t < 2 * N; ++t) o[t] = sc > 0.0 ? __double2float_rn(__ddiv_rn(del[t], sc)) : 0.0f;
-      double x = __dmul_rn(100.0, __ddiv_rn(sc, __dadd_rn(fabs(vals[N]), 1e-12)));
-      o[2 * N] = __double2float_rn(__ddiv_rn(x, __dadd_rn(1.0, x)));
+      for (int t = 0; t < 2 * N; ++t) o[t] = scf > 0.0f ? __fdiv_rn(__double2float_rn(del[t]), scf) : 0.0f;
+      const float den = __fadd_rn(__double2float_rn(fabs(vals[N])), 1e-12f);
+      const float x = __fmul_rn(100.0f, __fdiv_rn(scf, den));
+      o[2 * N] = __fdiv_rn(x, __fadd_rn(1.0f, x));
     }
   return true;
 }
