@@ -661,23 +661,35 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
           for (int v = 0; v < 5; ++v)
 #pragma unroll
             for (int e = 0; e < 3; ++e) acc[d][v][e] = T(0);
+        // time nodes in symmetric pairs (t, 3 - t): with w_{3-t} = w_t and
+        // L_e(1 - tau) = (-1)^e L_e(tau), the even modes take the sum of the
+        // pair's fluxes and the odd mode their difference
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          T qn[5], F[3][5];
+        for (int tp = 0; tp < 2; ++tp) {
+          T Fa[3][5], Fb[3][5];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            T x = swn[v * 64 + s];
+          for (int h = 0; h < 2; ++h) {
+            const int t = h ? 3 - tp : tp;
+            T qn[5];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
-            qn[v] = x;
+            for (int v = 0; v < 5; ++v) {
+              T x = swn[v * 64 + s];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
+              qn[v] = x;
+            }
+            if (h) phys_fluxes<3, T>(qn, gm1, Fb);
+            else phys_fluxes<3, T>(qn, gm1, Fa);
           }
-          phys_fluxes<3, T>(qn, gm1, F);
 #pragma unroll
           for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
-#pragma unroll
-              for (int e = 0; e < 3; ++e) acc[d][v][e] = fma(tc.WLT[e][t], F[d][v], acc[d][v][e]);
+            for (int v = 0; v < 5; ++v) {
+              const T sum = Fa[d][v] + Fb[d][v], dif = Fa[d][v] - Fb[d][v];
+              acc[d][v][0] = fma(tc.WLT[0][tp], sum, acc[d][v][0]);
+              acc[d][v][1] = fma(tc.WLT[1][tp], dif, acc[d][v][1]);
+              acc[d][v][2] = fma(tc.WLT[2][tp], sum, acc[d][v][2]);
+            }
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d)
