@@ -654,19 +654,19 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
         T pnk[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) pnk[c] = tb.PN[c][k];
-        T acc[3][5][3];
+        // time nodes in symmetric pairs (t, 3 - t): with w_{3-t} = w_t and
+        // L_e(1 - tau) = (-1)^e L_e(tau), the even modes take the sum of the
+        // pair's fluxes and the odd mode their difference.  The momentum flux
+        // rho v_d v_e is symmetric in (d, e): its three off-diagonal entries
+        // are formed and contracted once (12 distinct flux entries, not 15).
+        T aM[3][3], aD[3][3], aO[3][3], aE[3][3];   // mass, diagonal, off-diagonal, energy
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int v = 0; v < 5; ++v)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) acc[d][v][e] = T(0);
-        // time nodes in symmetric pairs (t, 3 - t): with w_{3-t} = w_t and
-        // L_e(1 - tau) = (-1)^e L_e(tau), the even modes take the sum of the
-        // pair's fluxes and the odd mode their difference
+          for (int e = 0; e < 3; ++e) aM[d][e] = aD[d][e] = aO[d][e] = aE[d][e] = T(0);
 #pragma unroll
         for (int tp = 0; tp < 2; ++tp) {
-          T Fa[3][5], Fb[3][5];
+          T f[2][12];   // per time point: mass[3], diag[3], off[3] (01, 02, 12), energy[3]
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int t = h ? 3 - tp : tp;
@@ -678,25 +678,55 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
               for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
               qn[v] = x;
             }
-            if (h) phys_fluxes<3, T>(qn, gm1, Fb);
-            else phys_fluxes<3, T>(qn, gm1, Fa);
+            const T irho = T(1) / qn[0];
+            T vel[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vel[d] = qn[1 + d] * irho;
+            T m2 = qn[1] * vel[0];
+            m2 = fma(qn[2], vel[1], m2);
+            m2 = fma(qn[3], vel[2], m2);
+            const T p = gm1 * (qn[4] - T(0.5) * m2);
+            const T Ep = qn[4] + p;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              f[h][d] = qn[1 + d];
+              f[h][3 + d] = fma(qn[1 + d], vel[d], p);
+              f[h][9 + d] = Ep * vel[d];
+            }
+            f[h][6] = qn[1] * vel[1];
+            f[h][7] = qn[1] * vel[2];
+            f[h][8] = qn[2] * vel[2];
           }
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              const T sum = Fa[d][v] + Fb[d][v], dif = Fa[d][v] - Fb[d][v];
-              acc[d][v][0] = fma(tc.WLT[0][tp], sum, acc[d][v][0]);
-              acc[d][v][1] = fma(tc.WLT[1][tp], dif, acc[d][v][1]);
-              acc[d][v][2] = fma(tc.WLT[2][tp], sum, acc[d][v][2]);
-            }
+          for (int k = 0; k < 3; ++k) {
+            T sum, dif;
+#define AWE_TPAIR(ACC, IDX)                                                   \
+            sum = f[0][IDX] + f[1][IDX];                                      \
+            dif = f[0][IDX] - f[1][IDX];                                      \
+            ACC[k][0] = fma(tc.WLT[0][tp], sum, ACC[k][0]);                   \
+            ACC[k][1] = fma(tc.WLT[1][tp], dif, ACC[k][1]);                   \
+            ACC[k][2] = fma(tc.WLT[2][tp], sum, ACC[k][2]);
+            AWE_TPAIR(aM, k)
+            AWE_TPAIR(aD, 3 + k)
+            AWE_TPAIR(aO, 6 + k)
+            AWE_TPAIR(aE, 9 + k)
+#undef AWE_TPAIR
+          }
         }
+        // Y1[d][v]: v = 0 mass, v = 1 + d diagonal momentum, v = 1 + e (e != d)
+        // the off-diagonal entry of the pair (d, e), v = 4 energy
+        // (the off-diagonal pair (d, c), d != c, is entry d + c - 1: 01, 02, 12)
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int v = 0; v < 5; ++v)
+          for (int e = 0; e < 3; ++e) {
+            Y1[((d * 5 + 0) * 64 + s) * 3 + e] = aM[d][e];
+            Y1[((d * 5 + 4) * 64 + s) * 3 + e] = aE[d][e];
+            Y1[((d * 5 + 1 + d) * 64 + s) * 3 + e] = aD[d][e];
 #pragma unroll
-            for (int e = 0; e < 3; ++e) Y1[((d * 5 + v) * 64 + s) * 3 + e] = acc[d][v][e];
+            for (int c = 0; c < 3; ++c)
+              if (c != d) Y1[((d * 5 + 1 + c) * 64 + s) * 3 + e] = aO[d + c - 1][e];
+          }
       }
       __syncwarp();
       fact_project<T, 2>(z, tb, ix, lane, lam);

@@ -104,9 +104,11 @@ def predictor_flops(D, N, picard):
             flops += 5 * 10 * 3 * 4 * 3                                # P3 (mul + FMA)
         for _ in range(1, picard):
             flops += 2 * (5 * 4 * 15 + 5 * 4 * 4 * 10 + 5 * 16 * 4 * 6)   # E1, E2, E3
-            # nodes: q and the fluxes at 4 time points, then the time contraction
-            # over the 2 symmetric pairs (sum and difference: 30 adds, 45 FMA)
-            flops += 64 * (4 * (2 * 5 * 3 + fn) + 2 * (30 + 2 * 45))
+            # nodes: q and the 12 distinct flux entries (the momentum flux is
+            # symmetric: 24 flops and a division) at 4 time points, then the
+            # time contraction over the 2 symmetric pairs (sum and difference:
+            # 24 adds, 36 FMA)
+            flops += 64 * (4 * (2 * 5 * 3 + 24) + 2 * (24 + 2 * 36))
             divs += 64 * 4 * fd
             flops += 2 * (3 * 5 * 16 * 6 * 4 + 3 * 5 * 4 * 10 * 4)        # P1, P2
             flops += 5 * 15 * 3 * 4 * 3                                     # P3
