@@ -612,41 +612,76 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
 #pragma unroll
             for (int c = 0; c < 3; ++c)
               cv[v][c] = *reinterpret_cast<const float4*>(C + (((v * 4 + i) * 4 + j) * 3 + c) * 4);
-          T acc[3][5][3];
+          // paired time nodes and the symmetric momentum flux, as in FP64
+          T aM[3][3], aD[3][3], aO[3][3], aE[3][3];
 #pragma unroll
           for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
+            for (int e = 0; e < 3; ++e) aM[d][e] = aD[d][e] = aO[d][e] = aE[d][e] = T(0);
 #pragma unroll
-              for (int e = 0; e < 3; ++e) acc[d][v][e] = T(0);
+          for (int tp = 0; tp < 2; ++tp) {
+            T f[2][12];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            T qn[5], F[3][5];
+            for (int h = 0; h < 2; ++h) {
+              const int t = h ? 3 - tp : tp;
+              T qn[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              T x = swn[v * 64 + s];
+              for (int v = 0; v < 5; ++v) {
+                T x = swn[v * 64 + s];
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float4 q4 = cv[v][c];
-                const T cc = t == 0 ? q4.x : t == 1 ? q4.y : t == 2 ? q4.z : q4.w;
-                x = fma(-cc, pnk[c], x);
+                for (int c = 0; c < 3; ++c) {
+                  const float4 q4 = cv[v][c];
+                  const T cc = t == 0 ? q4.x : t == 1 ? q4.y : t == 2 ? q4.z : q4.w;
+                  x = fma(-cc, pnk[c], x);
+                }
+                qn[v] = x;
               }
-              qn[v] = x;
+              const T irho = T(1) / qn[0];
+              T vel[3];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) vel[d] = qn[1 + d] * irho;
+              T m2 = qn[1] * vel[0];
+              m2 = fma(qn[2], vel[1], m2);
+              m2 = fma(qn[3], vel[2], m2);
+              const T p = gm1 * (qn[4] - T(0.5) * m2);
+              const T Ep = qn[4] + p;
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                f[h][d] = qn[1 + d];
+                f[h][3 + d] = fma(qn[1 + d], vel[d], p);
+                f[h][9 + d] = Ep * vel[d];
+              }
+              f[h][6] = qn[1] * vel[1];
+              f[h][7] = qn[1] * vel[2];
+              f[h][8] = qn[2] * vel[2];
             }
-            phys_fluxes<3, T>(qn, gm1, F);
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-              for (int v = 0; v < 5; ++v)
-#pragma unroll
-                for (int e = 0; e < 3; ++e) acc[d][v][e] = fma(tc.WLT[e][t], F[d][v], acc[d][v][e]);
+            for (int k2 = 0; k2 < 3; ++k2) {
+              T sum, dif;
+#define AWE_TPAIR(ACC, IDX)                                                   \
+              sum = f[0][IDX] + f[1][IDX];                                    \
+              dif = f[0][IDX] - f[1][IDX];                                    \
+              ACC[k2][0] = fma(tc.WLT[0][tp], sum, ACC[k2][0]);               \
+              ACC[k2][1] = fma(tc.WLT[1][tp], dif, ACC[k2][1]);               \
+              ACC[k2][2] = fma(tc.WLT[2][tp], sum, ACC[k2][2]);
+              AWE_TPAIR(aM, k2)
+              AWE_TPAIR(aD, 3 + k2)
+              AWE_TPAIR(aO, 6 + k2)
+              AWE_TPAIR(aE, 9 + k2)
+#undef AWE_TPAIR
+            }
           }
 #pragma unroll
           for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
+            for (int e = 0; e < 3; ++e) {
+              Y1[((d * 5 + 0) * 64 + s) * 3 + e] = aM[d][e];
+              Y1[((d * 5 + 4) * 64 + s) * 3 + e] = aE[d][e];
+              Y1[((d * 5 + 1 + d) * 64 + s) * 3 + e] = aD[d][e];
 #pragma unroll
-              for (int e = 0; e < 3; ++e) Y1[((d * 5 + v) * 64 + s) * 3 + e] = acc[d][v][e];
+              for (int c = 0; c < 3; ++c)
+                if (c != d) Y1[((d * 5 + 1 + c) * 64 + s) * 3 + e] = aO[d + c - 1][e];
+            }
         }
       } else
       for (int s = lane; s < 64; s += 32) {
