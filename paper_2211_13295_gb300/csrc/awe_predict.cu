@@ -376,6 +376,69 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   __syncwarp();
 }
 
+// Node stage of the Picard sweeps (factorised kernel): the fluxes of the
+// 4 time points of a node, time-contracted onto e = 0..2.  The time nodes are
+// taken in symmetric pairs (t, 3 - t): with w_{3-t} = w_t and L_e(1 - tau) =
+// (-1)^e L_e(tau), the even modes take the sum of the pair's fluxes and the
+// odd mode their difference.  The momentum flux rho v_d v_e is symmetric in
+// (d, e), so its three off-diagonal entries are formed and contracted once:
+// 12 distinct entries per state, f = mass[3], diagonal[3], off-diagonal[3]
+// (01, 02, 12), energy[3].
+template <typename T> struct NodeAcc {
+  T a[12][3];
+};
+
+template <typename T>
+__device__ __forceinline__ void sym_fluxes(const T* qn, T gm1, T* f) {
+  const T irho = T(1) / qn[0];
+  T vel[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) vel[d] = qn[1 + d] * irho;
+  T m2 = qn[1] * vel[0];
+  m2 = fma(qn[2], vel[1], m2);
+  m2 = fma(qn[3], vel[2], m2);
+  const T p = gm1 * (qn[4] - T(0.5) * m2);
+  const T Ep = qn[4] + p;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    f[d] = qn[1 + d];
+    f[3 + d] = fma(qn[1 + d], vel[d], p);
+    f[9 + d] = Ep * vel[d];
+  }
+  f[6] = qn[1] * vel[1];
+  f[7] = qn[1] * vel[2];
+  f[8] = qn[2] * vel[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void accumulate_pair(NodeAcc<T>& acc, const T* fa, const T* fb,
+                                                const Tabs<T>& tc, int tp) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const T sum = fa[k] + fb[k], dif = fa[k] - fb[k];
+    acc.a[k][0] = fma(tc.WLT[0][tp], sum, acc.a[k][0]);
+    acc.a[k][1] = fma(tc.WLT[1][tp], dif, acc.a[k][1]);
+    acc.a[k][2] = fma(tc.WLT[2][tp], sum, acc.a[k][2]);
+  }
+}
+
+// Y1[d][v][s][e]: v = 0 mass, v = 1 + d diagonal momentum, v = 1 + c (c != d)
+// the off-diagonal entry of the pair (d, c) (entry 6 + d + c - 1), v = 4 energy
+template <typename T>
+__device__ __forceinline__ void store_node_y1(T* Y1, int s, const NodeAcc<T>& acc) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      Y1[((d * 5 + 0) * 64 + s) * 3 + e] = acc.a[d][e];
+      Y1[((d * 5 + 4) * 64 + s) * 3 + e] = acc.a[9 + d][e];
+      Y1[((d * 5 + 1 + d) * 64 + s) * 3 + e] = acc.a[3 + d][e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c != d) Y1[((d * 5 + 1 + c) * 64 + s) * 3 + e] = acc.a[6 + d + c - 1][e];
+    }
+}
+
 template <typename T, int WPB>
 __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, const T* __restrict__ W,
                                                            const double* __restrict__ d_dt, int picard,
@@ -612,12 +675,7 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
 #pragma unroll
             for (int c = 0; c < 3; ++c)
               cv[v][c] = *reinterpret_cast<const float4*>(C + (((v * 4 + i) * 4 + j) * 3 + c) * 4);
-          // paired time nodes and the symmetric momentum flux, as in FP64
-          T aM[3][3], aD[3][3], aO[3][3], aE[3][3];
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) aM[d][e] = aD[d][e] = aO[d][e] = aE[d][e] = T(0);
+          NodeAcc<T> acc = {};
 #pragma unroll
           for (int tp = 0; tp < 2; ++tp) {
             T f[2][12];
@@ -636,52 +694,11 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
                 }
                 qn[v] = x;
               }
-              const T irho = T(1) / qn[0];
-              T vel[3];
-#pragma unroll
-              for (int d = 0; d < 3; ++d) vel[d] = qn[1 + d] * irho;
-              T m2 = qn[1] * vel[0];
-              m2 = fma(qn[2], vel[1], m2);
-              m2 = fma(qn[3], vel[2], m2);
-              const T p = gm1 * (qn[4] - T(0.5) * m2);
-              const T Ep = qn[4] + p;
-#pragma unroll
-              for (int d = 0; d < 3; ++d) {
-                f[h][d] = qn[1 + d];
-                f[h][3 + d] = fma(qn[1 + d], vel[d], p);
-                f[h][9 + d] = Ep * vel[d];
-              }
-              f[h][6] = qn[1] * vel[1];
-              f[h][7] = qn[1] * vel[2];
-              f[h][8] = qn[2] * vel[2];
+              sym_fluxes<T>(qn, gm1, f[h]);
             }
-#pragma unroll
-            for (int k2 = 0; k2 < 3; ++k2) {
-              T sum, dif;
-#define AWE_TPAIR(ACC, IDX)                                                   \
-              sum = f[0][IDX] + f[1][IDX];                                    \
-              dif = f[0][IDX] - f[1][IDX];                                    \
-              ACC[k2][0] = fma(tc.WLT[0][tp], sum, ACC[k2][0]);               \
-              ACC[k2][1] = fma(tc.WLT[1][tp], dif, ACC[k2][1]);               \
-              ACC[k2][2] = fma(tc.WLT[2][tp], sum, ACC[k2][2]);
-              AWE_TPAIR(aM, k2)
-              AWE_TPAIR(aD, 3 + k2)
-              AWE_TPAIR(aO, 6 + k2)
-              AWE_TPAIR(aE, 9 + k2)
-#undef AWE_TPAIR
-            }
+            accumulate_pair<T>(acc, f[0], f[1], tc, tp);
           }
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-              Y1[((d * 5 + 0) * 64 + s) * 3 + e] = aM[d][e];
-              Y1[((d * 5 + 4) * 64 + s) * 3 + e] = aE[d][e];
-              Y1[((d * 5 + 1 + d) * 64 + s) * 3 + e] = aD[d][e];
-#pragma unroll
-              for (int c = 0; c < 3; ++c)
-                if (c != d) Y1[((d * 5 + 1 + c) * 64 + s) * 3 + e] = aO[d + c - 1][e];
-            }
+          store_node_y1<T>(Y1, s, acc);
         }
       } else
       for (int s = lane; s < 64; s += 32) {
@@ -689,19 +706,10 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
         T pnk[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) pnk[c] = tb.PN[c][k];
-        // time nodes in symmetric pairs (t, 3 - t): with w_{3-t} = w_t and
-        // L_e(1 - tau) = (-1)^e L_e(tau), the even modes take the sum of the
-        // pair's fluxes and the odd mode their difference.  The momentum flux
-        // rho v_d v_e is symmetric in (d, e): its three off-diagonal entries
-        // are formed and contracted once (12 distinct flux entries, not 15).
-        T aM[3][3], aD[3][3], aO[3][3], aE[3][3];   // mass, diagonal, off-diagonal, energy
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-          for (int e = 0; e < 3; ++e) aM[d][e] = aD[d][e] = aO[d][e] = aE[d][e] = T(0);
+        NodeAcc<T> acc = {};
 #pragma unroll
         for (int tp = 0; tp < 2; ++tp) {
-          T f[2][12];   // per time point: mass[3], diag[3], off[3] (01, 02, 12), energy[3]
+          T f[2][12];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int t = h ? 3 - tp : tp;
@@ -713,55 +721,11 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
               for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
               qn[v] = x;
             }
-            const T irho = T(1) / qn[0];
-            T vel[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) vel[d] = qn[1 + d] * irho;
-            T m2 = qn[1] * vel[0];
-            m2 = fma(qn[2], vel[1], m2);
-            m2 = fma(qn[3], vel[2], m2);
-            const T p = gm1 * (qn[4] - T(0.5) * m2);
-            const T Ep = qn[4] + p;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              f[h][d] = qn[1 + d];
-              f[h][3 + d] = fma(qn[1 + d], vel[d], p);
-              f[h][9 + d] = Ep * vel[d];
-            }
-            f[h][6] = qn[1] * vel[1];
-            f[h][7] = qn[1] * vel[2];
-            f[h][8] = qn[2] * vel[2];
+            sym_fluxes<T>(qn, gm1, f[h]);
           }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            T sum, dif;
-#define AWE_TPAIR(ACC, IDX)                                                   \
-            sum = f[0][IDX] + f[1][IDX];                                      \
-            dif = f[0][IDX] - f[1][IDX];                                      \
-            ACC[k][0] = fma(tc.WLT[0][tp], sum, ACC[k][0]);                   \
-            ACC[k][1] = fma(tc.WLT[1][tp], dif, ACC[k][1]);                   \
-            ACC[k][2] = fma(tc.WLT[2][tp], sum, ACC[k][2]);
-            AWE_TPAIR(aM, k)
-            AWE_TPAIR(aD, 3 + k)
-            AWE_TPAIR(aO, 6 + k)
-            AWE_TPAIR(aE, 9 + k)
-#undef AWE_TPAIR
-          }
+          accumulate_pair<T>(acc, f[0], f[1], tc, tp);
         }
-        // Y1[d][v]: v = 0 mass, v = 1 + d diagonal momentum, v = 1 + e (e != d)
-        // the off-diagonal entry of the pair (d, e), v = 4 energy
-        // (the off-diagonal pair (d, c), d != c, is entry d + c - 1: 01, 02, 12)
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-          for (int e = 0; e < 3; ++e) {
-            Y1[((d * 5 + 0) * 64 + s) * 3 + e] = aM[d][e];
-            Y1[((d * 5 + 4) * 64 + s) * 3 + e] = aE[d][e];
-            Y1[((d * 5 + 1 + d) * 64 + s) * 3 + e] = aD[d][e];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              if (c != d) Y1[((d * 5 + 1 + c) * 64 + s) * 3 + e] = aO[d + c - 1][e];
-          }
+        store_node_y1<T>(Y1, s, acc);
       }
       __syncwarp();
       fact_project<T, 2>(z, tb, ix, lane, lam);
