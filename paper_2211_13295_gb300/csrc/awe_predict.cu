@@ -27,6 +27,19 @@ namespace awe {
 // ---------------------------------------------------------------------------
 // direct predictor
 // ---------------------------------------------------------------------------
+// whether space-time mode b (degree <= N-1, time exponent outermost) has an
+// odd time exponent
+template <int D, int N> __host__ __device__ constexpr bool st_time_odd(int b) {
+  int idx = 0;
+  for (int e = 0; e <= N - 1; ++e) {
+    const int K = N - 1 - e;
+    const int cnt = D == 3 ? (K + 1) * (K + 2) * (K + 3) / 6 : (K + 1) * (K + 2) / 2;
+    if (b < idx + cnt) return (e & 1) != 0;
+    idx += cnt;
+  }
+  return false;
+}
+
 template <int D, int N, typename T>
 __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const T* __restrict__ W,
                                                         const double* __restrict__ d_dt, int picard,
@@ -98,27 +111,40 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
             for (int m = 0; m < NS; ++m) acc = fma(w[v][m], WS[s * NS + m], acc);
             wn[v] = acc;
           }
-          for (int t = 0; t < NN; ++t) {
-            const int node = s * NN + t;
-            const T* ev = EV + (long long)node * NG;
-            T qn[NV];
+          // time nodes in symmetric pairs (t, NN-1-t): the projection kernel of
+          // the second is (-1)^e times that of the first (symmetric weights,
+          // L_e(1 - tau) = (-1)^e L_e(tau)), so a pair enters through the sum
+          // of its fluxes (even e) or their difference (odd e); with NN odd
+          // the middle node enters alone
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              T acc = wn[v];
+          for (int t = 0; t < (NN + 1) / 2; ++t) {
+            const int t2 = NN - 1 - t;
+            T Fa[D][D + 2], Fb[D][D + 2];
 #pragma unroll
-              for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], ev[b], acc);
-              qn[v] = acc;
-            }
-            T F[D][D + 2];
-            phys_fluxes<D, T>(qn, gm1, F);
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              const T* kp = KP + ((long long)d * (NSN * NN) + node) * NG;
+            for (int h = 0; h < 2; ++h) {
+              if (h == 1 && t2 == t) break;
+              const int node = s * NN + (h ? t2 : t);
+              const T* ev = EV + (long long)node * NG;
+              T qn[NV];
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
-                T f = lam[d] * F[d][v];
+                T acc = wn[v];
 #pragma unroll
-                for (int b = 0; b < NG; ++b) gn[v][b] = fma(f, kp[b], gn[v][b]);
+                for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], ev[b], acc);
+                qn[v] = acc;
+              }
+              if (h) phys_fluxes<D, T>(qn, gm1, Fb);
+              else phys_fluxes<D, T>(qn, gm1, Fa);
+            }
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              const T* kp = KP + ((long long)d * (NSN * NN) + s * NN + t) * NG;
+#pragma unroll
+              for (int v = 0; v < NV; ++v) {
+                const T fs = t2 != t ? lam[d] * (Fa[d][v] + Fb[d][v]) : lam[d] * Fa[d][v];
+                const T fd = t2 != t ? lam[d] * (Fa[d][v] - Fb[d][v]) : fs;
+#pragma unroll
+                for (int b = 0; b < NG; ++b) gn[v][b] = fma(st_time_odd<D, N>(b) ? fd : fs, kp[b], gn[v][b]);
               }
             }
           }

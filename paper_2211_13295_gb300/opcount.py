@@ -129,9 +129,14 @@ def predictor_flops(D, N, picard):
     if picard >= 1:
         flops += NSN * (2 * nv * NS + fn + D * nv * (1 + 2 * NG0))
         divs += NSN * fd
+    npair, nmid = NN // 2, NN % 2
     for _ in range(1, picard):
         flops += NSN * 2 * nv * NS
-        flops += NSN * NN * (2 * nv * NG + fn + D * nv * (1 + 2 * NG))
+        flops += NSN * NN * (2 * nv * NG + fn)
+        # time contraction: a symmetric pair of time nodes enters through the
+        # sum and the difference of its scaled fluxes (2 adds, 2 mul, NG FMA
+        # per flux entry), the middle node of an odd rule alone (1 mul, NG FMA)
+        flops += NSN * D * nv * (npair * (4 + 2 * NG) + nmid * (1 + 2 * NG))
         divs += NSN * NN * fd
     flops += D * 2 * NFQ * nv * 2 * (NS + NG)
     return flops, divs
