@@ -40,6 +40,83 @@ template <int D, int N> __host__ __device__ constexpr bool st_time_odd(int b) {
   return false;
 }
 
+// compile-time positions in the mode enumerations of the tables: spatial
+// modes (a, b, c) of total degree <= N with c outermost, then b, then a;
+// space-time modes (a, b, c, e) of total degree <= M with e outermost
+template <int D, int N> __host__ __device__ constexpr int sp_index(int a, int b, int c) {
+  int idx = 0;
+  for (int cc = 0; cc <= (D == 3 ? N : 0); ++cc)
+    for (int bb = 0; bb <= N - cc; ++bb)
+      for (int aa = 0; aa <= N - bb - cc; ++aa) {
+        if (aa == a && bb == b && cc == c) return idx;
+        ++idx;
+      }
+  return -1;
+}
+template <int D, int M> __host__ __device__ constexpr int st_index(int a, int b, int c, int e) {
+  int idx = 0;
+  for (int ee = 0; ee <= M; ++ee)
+    for (int cc = 0; cc <= (D == 3 ? M - ee : 0); ++cc)
+      for (int bb = 0; bb <= M - ee - cc; ++bb)
+        for (int aa = 0; aa <= M - ee - bb - cc; ++aa) {
+          if (aa == a && bb == b && cc == c && ee == e) return idx;
+          ++idx;
+        }
+  return -1;
+}
+// exponent k (0 = a, 1 = b, 2 = c, 3 = e) of space-time mode i
+template <int D, int M> __host__ __device__ constexpr int st_exp(int i, int k) {
+  int idx = 0;
+  for (int ee = 0; ee <= M; ++ee)
+    for (int cc = 0; cc <= (D == 3 ? M - ee : 0); ++cc)
+      for (int bb = 0; bb <= M - ee - cc; ++bb)
+        for (int aa = 0; aa <= M - ee - bb - cc; ++aa) {
+          if (idx == i) return k == 0 ? aa : k == 1 ? bb : k == 2 ? cc : ee;
+          ++idx;
+        }
+  return -1;
+}
+
+// Mass row of the new G (thread-per-zone form).  The mass flux of direction d
+// is the momentum q_{1+d} = w_{1+d} - sum_g g_{1+d} P P (P) I_e(tau), of total
+// degree <= N: the N+1-point Gauss rules integrate its products with the test
+// functions exactly, so its projection is itself and the G coefficient is its
+// exact derivative, from I_0 = (L_0 + L_1)/2, I_e = (L_{e+1} - L_{e-1}) /
+// (2(2e+1)) and dP1 = P0, dP2 = 2 P1, dP3 = 3 P2 + P0/10.  Same value as
+// projecting the node fluxes, up to rounding, without the node work.
+template <int D, int N, typename T>
+__device__ __forceinline__ T mass_gmode_direct(const T (*w)[Modes<D, N>::NS], const T (*g)[Modes<D, N>::NG],
+                                               const T* lam, int b) {
+  const int e = st_exp<D, N - 1>(b, 3);
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      int ix[3] = {st_exp<D, N - 1>(b, 0), st_exp<D, N - 1>(b, 1), D == 3 ? st_exp<D, N - 1>(b, 2) : 0};
+      const int ad = ix[d];
+      if (k == 1 && ad != 0) break;
+      ix[d] = k == 0 ? ad + 1 : 3;
+      const int deg = ix[0] + ix[1] + ix[2];
+      if (deg + e > N) continue;
+      const T f = k == 0 ? T(ad + 1) : T(0.1);   // coefficient of P_ad in dP_{a'}
+      // coefficient of L_e of the momentum's mode ix
+      T gg[3];
+#pragma unroll
+      for (int ee = 0; ee < 3; ++ee)
+        gg[ee] = deg + ee <= N - 1 ? g[1 + d][st_index<D, N - 1>(ix[0], ix[1], ix[2], ee)] : T(0);
+      T m;
+      if (e == 0) m = fma(T(1.0 / 6.0), gg[1], fma(T(-0.5), gg[0], w[1 + d][sp_index<D, N>(ix[0], ix[1], ix[2])]));
+      else if (e == 1) m = fma(T(0.1), gg[2], T(-0.5) * gg[0]);
+      else m = T(-1.0 / 6.0) * gg[1];
+      s = fma(f, m, s);
+    }
+    acc = fma(lam[d], s, acc);
+  }
+  return acc;
+}
+
 template <int D, int N, typename T>
 __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const T* __restrict__ W,
                                                         const double* __restrict__ d_dt, int picard,
@@ -73,7 +150,10 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
 #pragma unroll
       for (int b = 0; b < NG; ++b) g[v][b] = T(0);
     if (picard >= 1) {
-      // sweep 0: time-independent flux at the spatial nodes
+      // sweep 0: time-independent flux at the spatial nodes (momentum and
+      // energy rows; the mass row from the momentum's coefficients, g = 0)
+#pragma unroll
+      for (int b = 0; b < NG0; ++b) g[0][b] = mass_gmode_direct<D, N, T>(w, g, lam, b);
       for (int s = 0; s < NSN; ++s) {
         T qn[NV];
 #pragma unroll
@@ -89,7 +169,7 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
         for (int d = 0; d < D; ++d) {
           const T* ks = KS + ((long long)d * NSN + s) * NG;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
+          for (int v = 1; v < NV; ++v) {
             T f = lam[d] * F[d][v];
 #pragma unroll
             for (int b = 0; b < NG0; ++b) g[v][b] = fma(f, ks[b], g[v][b]);
@@ -99,7 +179,9 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
       for (int sweep = 1; sweep < picard; ++sweep) {
         T gn[NV][NG];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
+        for (int b = 0; b < NG; ++b) gn[0][b] = mass_gmode_direct<D, N, T>(w, g, lam, b);
+#pragma unroll
+        for (int v = 1; v < NV; ++v)
 #pragma unroll
           for (int b = 0; b < NG; ++b) gn[v][b] = T(0);
         for (int s = 0; s < NSN; ++s) {
@@ -140,7 +222,7 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
             for (int d = 0; d < D; ++d) {
               const T* kp = KP + ((long long)d * (NSN * NN) + s * NN + t) * NG;
 #pragma unroll
-              for (int v = 0; v < NV; ++v) {
+              for (int v = 1; v < NV; ++v) {
                 const T fs = t2 != t ? lam[d] * (Fa[d][v] + Fb[d][v]) : lam[d] * Fa[d][v];
                 const T fd = t2 != t ? lam[d] * (Fa[d][v] - Fb[d][v]) : fs;
 #pragma unroll
@@ -201,13 +283,17 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
 // factorised predictor, 3D, N = 3: one warp per zone
 // ---------------------------------------------------------------------------
 template <typename T> struct FactSmem {
-  // per-zone layout (elements of T)
-  static constexpr int W = 0;                  // w[5][20]
-  static constexpr int WN = W + 100;           // wn[5][64]
-  static constexpr int G = WN + 320;           // g[5][15]
-  static constexpr int R1 = sizeof(T) == 4 ? G + 76 : G + 75;   // (FP32: 16-byte aligned C rows)
-  static constexpr int R2 = R1 + 1080;         // A/B, Y1 (2880)
-  static constexpr int SIZE = R2 + 2880;       // 4455 (FP64), 4456 (FP32)
+  // per-zone layout (elements of T).  w at the spatial nodes: every stage that
+  // reads it is lane-static in the node (s = lane, lane + 32), so FP64 keeps
+  // it in registers (its shared memory sets its occupancy); FP32 keeps it here
+  // (its registers set its occupancy)
+  static constexpr bool WN_REG = sizeof(T) == 8;
+  static constexpr int W = 0;                          // w[5][20]
+  static constexpr int WN = W + 100;                   // wn[5][64] (FP32)
+  static constexpr int G = WN + (WN_REG ? 0 : 320);    // g[5][15]
+  static constexpr int R1 = WN_REG ? G + 75 : G + 76;  // (FP32: 16-byte aligned C rows)
+  static constexpr int R2 = R1 + 960;                  // A/B, Y1 (2304)
+  static constexpr int SIZE = R2 + 2304;               // 3439 (FP64), 3760 (FP32)
 };
 
 // index tables copied to shared memory once per block (lane-divergent reads
@@ -215,6 +301,11 @@ template <typename T> struct FactSmem {
 struct FactIdx {
   int8_t sm3[20][3], pair3[10][2], tri2[10][3], pair2[6][2], gm[15][4];
   int8_t gidx[3][3][3][3], tri_idx[3][3][3], pair2_idx[3][3], pair3_idx[4][4], sm3_idx[4][4][4];
+  // sources of the mass row of G (mass_gmode), per direction d and G-mode b:
+  // [0] w, [1..3] g with e = 0..2 of the momentum mode one degree up in d
+  // (offsets into the w / g rows, 255 = none), [4] w of the mode three degrees
+  // up (b = 0 only), [5] the derivative factor of the first (1, 2 or 3)
+  uint8_t mass_src[3][6][16];
 };
 __constant__ FactIdx c_fidx;
 
@@ -270,15 +361,55 @@ __host__ __device__ constexpr int tri2_r(int t) {
 __host__ __device__ constexpr int pair2_p(int pe) { return pe < 3 ? pe : pe < 5 ? pe - 3 : 0; }
 __host__ __device__ constexpr int pair2_e(int pe) { return pe < 3 ? 0 : pe < 5 ? 1 : 2; }
 
+// Mass row of the new G.  The mass flux of direction d is the momentum
+// q_{1+d} = w_{1+d} - sum_g g_{1+d} P_a P_b P_c I_e(tau): a polynomial of total
+// degree <= 3 in (x, y, z, tau), the space the fluxes are projected onto.  The
+// Gauss rules of the projection (4 points per axis) integrate its products with
+// the test functions exactly, so the projection is the polynomial itself and
+// its derivative follows from the coefficients: I_0 = (L_0 + L_1)/2,
+// I_e = (L_{e+1} - L_{e-1}) / (2(2e+1)), dP1 = P0, dP2 = 2 P1, dP3 = 3 P2 + P0/10.
+// Same value as projecting the node fluxes, up to rounding, without the node
+// work.  Branch-free over a source table (FactIdx::mass_src), so lanes with
+// different G-modes do not diverge.  Reads the previous G (rows 1..3) and w.
+template <typename T>
+__device__ __forceinline__ T mass_gmode(const T* z, const FactIdx& ix, int b, const T lam[3]) {
+  const int e = ix.gm[b][3];
+  const T* zw = z + FactSmem<T>::W;
+  const T* zg = z + FactSmem<T>::G;
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ow = ix.mass_src[d][0][b], o0 = ix.mass_src[d][1][b], o1 = ix.mass_src[d][2][b];
+    const int o2 = ix.mass_src[d][3][b], o3 = ix.mass_src[d][4][b];
+    const T w = ow != 255 ? zw[ow] : T(0);
+    const T g0 = o0 != 255 ? zg[o0] : T(0);
+    const T g1 = o1 != 255 ? zg[o1] : T(0);
+    const T g2 = o2 != 255 ? zg[o2] : T(0);
+    const T w3 = o3 != 255 ? zw[o3] : T(0);
+    // coefficient of L_e of the source mode
+    const T m0 = fma(T(1.0 / 6.0), g1, fma(T(-0.5), g0, w));
+    const T m1 = fma(T(0.1), g2, T(-0.5) * g0);
+    const T m2 = T(-1.0 / 6.0) * g1;
+    const T m = e == 0 ? m0 : e == 1 ? m1 : m2;
+    const T sd = fma(T(ix.mass_src[d][5][b]), m, T(0.1) * w3);
+    acc = fma(lam[d], sd, acc);
+  }
+  return acc;
+}
+
+// Picard projection of the node fluxes of the momentum and energy rows (the
+// mass row by mass_gmode).  Y1 rows v' = 0..3 hold the variables 1..4.
 template <typename T, int EMAX>
 __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const FactIdx& ix, int lane,
                                              const T lam[3]) {
   constexpr int NPE = EMAX == 0 ? 3 : 6;     // (p,e) pairs with e <= EMAX
   constexpr int NTR = EMAX == 0 ? 6 : 10;    // (p,q,e) triples with e <= EMAX
   constexpr int NGE = EMAX == 0 ? 10 : 15;   // G-modes with e <= EMAX
-  const T* Y1 = z + FactSmem<T>::R2;         // [d][v][s][e3]  (e3 stride 3)
-  T* Y2 = z + FactSmem<T>::R1;               // [v][n2][pe]    one direction (pe stride 6)
-  T* Y3 = z + FactSmem<T>::R1 + 480;         // [d][v][n1][tri] (tri stride 10)
+  const T* Y1 = z + FactSmem<T>::R2;         // [d][v'][s][e3]  (e3 stride 3)
+  T* Y2 = z + FactSmem<T>::R1;               // [v'][n2][pe]    one direction (pe stride 6)
+  T* Y3 = z + FactSmem<T>::R1 + 384;         // [d][v'][n1][tri] (tri stride 10)
+  // the mass row from the previous G, before P3 overwrites it
+  const T gmass = lane < NGE ? mass_gmode<T>(z, ix, lane, lam) : T(0);
   // one direction at a time: P1 contracts the first dimension (z for d = x,
   // y; y for d = z), P2 the second (y for d = x; x for d = y, z).  Static lane
   // mappings (kStatic): P1 lanes own (n2, half of the (p,e) pairs), P2 lanes
@@ -289,15 +420,15 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   for (int d = 0; d < 3; ++d) {
     if constexpr ((kStatic<T> & kStP1) != 0) {
       {
-        // lanes own (n2, a group of variables: 0-2 or 3-4) and compute every
-        // (p,e) pair of a variable from its 4 x (EMAX+1) values, loaded once
+        // lanes own (n2, a pair of rows: 0-1 or 2-3) and compute every (p,e)
+        // pair of a row from its 4 x (EMAX+1) values, loaded once
         const int n2 = lane & 15, vh = lane >> 4;
         const int a0 = n2 & 3, a1 = n2 >> 2;
         const int sbase = d < 2 ? (a0 + 4 * a1) : (a0 + 16 * a1);
         const int sstr = d < 2 ? 16 : 4;
-        const T* y1 = Y1 + (d * 5) * 64 * 3;
+        const T* y1 = Y1 + (d * 4) * 64 * 3;
 #pragma unroll 1
-        for (int v = 3 * vh; v < (vh ? 5 : 3); ++v) {
+        for (int v = 2 * vh; v < 2 * vh + 2; ++v) {
           const T* yv = y1 + v * 64 * 3 + sbase * 3;
           T y[EMAX + 1][4];
 #pragma unroll
@@ -316,7 +447,7 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
       }
     } else {
 #pragma unroll 2
-      for (int it = lane; it < 5 * 16 * NPE; it += 32) {
+      for (int it = lane; it < 4 * 16 * NPE; it += 32) {
         int pe = it % NPE;
         int rest = it / NPE;
         int n2 = rest % 16;
@@ -328,14 +459,14 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
         for (int m = 0; m < 4; ++m) {
           // d < 2: n2 = (i,j), sum over k; d = 2: n2 = (i,k), sum over j
           int s = d < 2 ? (a0 + 4 * a1 + 16 * m) : (a0 + 4 * m + 16 * a1);
-          acc = fma(Y1[((d * 5 + v) * 64 + s) * 3 + e], tb.WPN[p][m], acc);
+          acc = fma(Y1[((d * 4 + v) * 64 + s) * 3 + e], tb.WPN[p][m], acc);
         }
         Y2[(v * 16 + n2) * 6 + pe] = acc;
       }
     }
     __syncwarp();
     if constexpr ((kStatic<T> & kStP2) != 0) {
-      if (lane < 20) {
+      if (lane < 16) {
         const int n1 = lane & 3, v = lane >> 2;
         const int nbase = d == 0 ? n1 : 4 * n1;
         const int nstr = d == 0 ? 4 : 1;
@@ -353,13 +484,13 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
             T acc = T(0);
 #pragma unroll
             for (int m = 0; m < 4; ++m) acc = fma(y[pe][m], tc.WPN[p][m], acc);
-            Y3[((d * 5 + v) * 4 + n1) * 10 + tri2idx(p, qq, e)] = acc;
+            Y3[((d * 4 + v) * 4 + n1) * 10 + tri2idx(p, qq, e)] = acc;
           }
         }
       }
     } else {
 #pragma unroll 2
-      for (int it = lane; it < 5 * 4 * NTR; it += 32) {
+      for (int it = lane; it < 4 * 4 * NTR; it += 32) {
         int tr = it % NTR;
         int rest = it / NTR;
         int n1 = rest % 4;
@@ -375,13 +506,13 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
           int n2 = d == 0 ? (n1 + 4 * m) : (m + 4 * n1);
           acc = fma(Y2[(v * 16 + n2) * 6 + pe], tb.WPN[p][m], acc);
         }
-        Y3[((d * 5 + v) * 4 + n1) * 10 + tr] = acc;
+        Y3[((d * 4 + v) * 4 + n1) * 10 + tr] = acc;
       }
     }
     __syncwarp();
   }
   // P3: contract the derivative dimension with the Q factors, sum over d
-  for (int it = lane; it < 5 * NGE; it += 32) {
+  for (int it = lane; it < 4 * NGE; it += 32) {
     int b = it % NGE;
     int v = it / NGE;
     int a = ix.gm[b][0], bb = ix.gm[b][1], c = ix.gm[b][2], e = ix.gm[b][3];
@@ -390,12 +521,13 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
     int t0 = ix.tri_idx[bb][c][e], t1 = ix.tri_idx[a][c][e], t2 = ix.tri_idx[a][bb][e];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      s0 = fma(Y3[((0 * 5 + v) * 4 + m) * 10 + t0], tb.QN[a][slack][m], s0);
-      s1 = fma(Y3[((1 * 5 + v) * 4 + m) * 10 + t1], tb.QN[bb][slack][m], s1);
-      s2 = fma(Y3[((2 * 5 + v) * 4 + m) * 10 + t2], tb.QN[c][slack][m], s2);
+      s0 = fma(Y3[((0 * 4 + v) * 4 + m) * 10 + t0], tb.QN[a][slack][m], s0);
+      s1 = fma(Y3[((1 * 4 + v) * 4 + m) * 10 + t1], tb.QN[bb][slack][m], s1);
+      s2 = fma(Y3[((2 * 4 + v) * 4 + m) * 10 + t2], tb.QN[c][slack][m], s2);
     }
-    z[FactSmem<T>::G + v * 15 + b] = fma(lam[0], s0, fma(lam[1], s1, lam[2] * s2));
+    z[FactSmem<T>::G + (v + 1) * 15 + b] = fma(lam[0], s0, fma(lam[1], s1, lam[2] * s2));
   }
+  if (lane < NGE) z[FactSmem<T>::G + lane] = gmass;
   if (EMAX == 0) {
     for (int it = lane; it < 5 * 5; it += 32) z[FactSmem<T>::G + (it / 5) * 15 + 10 + it % 5] = T(0);
   }
@@ -407,11 +539,11 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
 // taken in symmetric pairs (t, 3 - t): with w_{3-t} = w_t and L_e(1 - tau) =
 // (-1)^e L_e(tau), the even modes take the sum of the pair's fluxes and the
 // odd mode their difference.  The momentum flux rho v_d v_e is symmetric in
-// (d, e), so its three off-diagonal entries are formed and contracted once:
-// 12 distinct entries per state, f = mass[3], diagonal[3], off-diagonal[3]
-// (01, 02, 12), energy[3].
+// (d, e), so its three off-diagonal entries are formed and contracted once;
+// the mass fluxes are not needed (mass_gmode): 9 entries per state,
+// f = diagonal[3], off-diagonal[3] (01, 02, 12), energy[3].
 template <typename T> struct NodeAcc {
-  T a[12][3];
+  T a[9][3];
 };
 
 template <typename T>
@@ -427,20 +559,19 @@ __device__ __forceinline__ void sym_fluxes(const T* qn, T gm1, T* f) {
   const T Ep = qn[4] + p;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    f[d] = qn[1 + d];
-    f[3 + d] = fma(qn[1 + d], vel[d], p);
-    f[9 + d] = Ep * vel[d];
+    f[d] = fma(qn[1 + d], vel[d], p);
+    f[6 + d] = Ep * vel[d];
   }
-  f[6] = qn[1] * vel[1];
-  f[7] = qn[1] * vel[2];
-  f[8] = qn[2] * vel[2];
+  f[3] = qn[1] * vel[1];
+  f[4] = qn[1] * vel[2];
+  f[5] = qn[2] * vel[2];
 }
 
 template <typename T>
 __device__ __forceinline__ void accumulate_pair(NodeAcc<T>& acc, const T* fa, const T* fb,
                                                 const Tabs<T>& tc, int tp) {
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
+  for (int k = 0; k < 9; ++k) {
     const T sum = fa[k] + fb[k], dif = fa[k] - fb[k];
     acc.a[k][0] = fma(tc.WLT[0][tp], sum, acc.a[k][0]);
     acc.a[k][1] = fma(tc.WLT[1][tp], dif, acc.a[k][1]);
@@ -448,20 +579,20 @@ __device__ __forceinline__ void accumulate_pair(NodeAcc<T>& acc, const T* fa, co
   }
 }
 
-// Y1[d][v][s][e]: v = 0 mass, v = 1 + d diagonal momentum, v = 1 + c (c != d)
-// the off-diagonal entry of the pair (d, c) (entry 6 + d + c - 1), v = 4 energy
+// Y1[d][v'][s][e] for the variables 1 + v': v' = d diagonal momentum, v' = c
+// (c != d) the off-diagonal entry of the pair (d, c) (entry 3 + d + c - 1),
+// v' = 3 energy
 template <typename T>
 __device__ __forceinline__ void store_node_y1(T* Y1, int s, const NodeAcc<T>& acc) {
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      Y1[((d * 5 + 0) * 64 + s) * 3 + e] = acc.a[d][e];
-      Y1[((d * 5 + 4) * 64 + s) * 3 + e] = acc.a[9 + d][e];
-      Y1[((d * 5 + 1 + d) * 64 + s) * 3 + e] = acc.a[3 + d][e];
+      Y1[((d * 4 + 3) * 64 + s) * 3 + e] = acc.a[6 + d][e];
+      Y1[((d * 4 + d) * 64 + s) * 3 + e] = acc.a[d][e];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c != d) Y1[((d * 5 + 1 + c) * 64 + s) * 3 + e] = acc.a[6 + d + c - 1][e];
+        if (c != d) Y1[((d * 4 + c) * 64 + s) * 3 + e] = acc.a[3 + d + c - 1][e];
     }
 }
 
@@ -496,7 +627,8 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
   const T* FG = tab + L.fg;
   for (long long r = (long long)blockIdx.x * WPB + wib; r < nb; r += (long long)gridDim.x * WPB) {
     T* sw = z + FactSmem<T>::W;
-    T* swn = z + FactSmem<T>::WN;
+    T* swn = z + FactSmem<T>::WN;          // FP32
+    T wnr[2][5];                            // FP64: w at the nodes s = lane, lane + 32
     T* sg = z + FactSmem<T>::G;
     for (int it = lane; it < 100; it += 32) sw[it] = W[(long long)it * nb + r];
     __syncwarp();
@@ -560,14 +692,18 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
           T2[it] = acc;
         }
         __syncwarp();
-#pragma unroll 2
-        for (int it = lane; it < 320; it += 32) {
-          int s = it % 64, v = it / 64;
-          int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
-          T acc = T(0);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc = fma(T2[((v * 4 + i) * 4 + j) * 4 + c], tb.PN[c][k], acc);
-          swn[v * 64 + s] = acc;
+        for (int hs = 0; hs < 2; ++hs) {
+          const int s = lane + 32 * hs;
+          const int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc = fma(T2[((v * 4 + i) * 4 + j) * 4 + c], tb.PN[c][k], acc);
+            if constexpr (FactSmem<T>::WN_REG) wnr[hs][v] = acc;
+            else swn[v * 64 + s] = acc;
+          }
         }
       }
       __syncwarp();
@@ -577,15 +713,17 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
     T* Y1 = z + FactSmem<T>::R2;
     if (picard >= 1) {
       // sweep 0: flux at the spatial nodes, time-independent
-      for (int s = lane; s < 64; s += 32) {
+#pragma unroll
+      for (int hs = 0; hs < 2; ++hs) {
+        const int s = lane + 32 * hs;
         T qn[5], F[3][5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) qn[v] = swn[v * 64 + s];
+        for (int v = 0; v < 5; ++v) qn[v] = FactSmem<T>::WN_REG ? wnr[hs][v] : swn[v * 64 + s];
         phys_fluxes<3, T>(qn, gm1, F);
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int v = 0; v < 5; ++v) Y1[((d * 5 + v) * 64 + s) * 3 + 0] = F[d][v];
+          for (int v = 1; v < 5; ++v) Y1[((d * 4 + v - 1) * 64 + s) * 3 + 0] = F[d][v];
       }
       __syncwarp();
       fact_project<T, 0>(z, tb, ix, lane, lam);
@@ -704,7 +842,7 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
           NodeAcc<T> acc = {};
 #pragma unroll
           for (int tp = 0; tp < 2; ++tp) {
-            T f[2][12];
+            T f[2][9];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int t = h ? 3 - tp : tp;
@@ -727,7 +865,9 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
           store_node_y1<T>(Y1, s, acc);
         }
       } else
-      for (int s = lane; s < 64; s += 32) {
+#pragma unroll 1
+      for (int hs = 0; hs < 2; ++hs) {
+        const int s = lane + 32 * hs;
         int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
         T pnk[3];
 #pragma unroll
@@ -735,14 +875,14 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
         NodeAcc<T> acc = {};
 #pragma unroll
         for (int tp = 0; tp < 2; ++tp) {
-          T f[2][12];
+          T f[2][9];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int t = h ? 3 - tp : tp;
             T qn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              T x = swn[v * 64 + s];
+              T x = FactSmem<T>::WN_REG ? (hs ? wnr[1][v] : wnr[0][v]) : swn[v * 64 + s];
 #pragma unroll
               for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
               qn[v] = x;
@@ -898,6 +1038,32 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
     for (int t = 0; t < 4; ++t) h.gm[b][t] = (int8_t)g[b][t];
     h.gidx[g[b][0]][g[b][1]][g[b][2]][g[b][3]] = b;
   }
+  // mass-row sources (mass_gmode): the momentum mode one degree up in d, and
+  // for b = 0 the mode three degrees up (dP3 = 3 P2 + P0/10)
+  memset(h.mass_src, 255, sizeof(h.mass_src));
+  for (int d = 0; d < 3; ++d)
+    for (int b = 0; b < 16; ++b) h.mass_src[d][5][b] = 0;
+  for (int b = 0; b < 15; ++b) {
+    const int e = g[b][3];
+    for (int d = 0; d < 3; ++d) {
+      for (int k = 0; k < 2; ++k) {
+        int abc[3] = {g[b][0], g[b][1], g[b][2]};
+        const int ad = abc[d];
+        if (k == 1 && ad != 0) break;
+        abc[d] = k == 0 ? ad + 1 : 3;
+        const int deg = abc[0] + abc[1] + abc[2];
+        if (deg + e > 3) continue;
+        if (k == 1) {
+          h.mass_src[d][4][b] = (uint8_t)((1 + d) * 20 + h.sm3_idx[abc[0]][abc[1]][abc[2]]);
+          continue;
+        }
+        h.mass_src[d][5][b] = (uint8_t)(ad + 1);
+        h.mass_src[d][0][b] = (uint8_t)((1 + d) * 20 + h.sm3_idx[abc[0]][abc[1]][abc[2]]);
+        for (int ee = 0; ee < 3; ++ee)
+          if (deg + ee <= 2) h.mass_src[d][1 + ee][b] = (uint8_t)((1 + d) * 15 + h.gidx[abc[0]][abc[1]][abc[2]][ee]);
+      }
+    }
+  }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_fidx, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
@@ -907,7 +1073,7 @@ template <typename T> static size_t fact_smem(int wpb) {
   return ((sizeof(Tabs<T>) + 15) / 16) * 16 + ((sizeof(FactIdx) + 15) / 16) * 16 +
          (size_t)wpb * FactSmem<T>::SIZE * sizeof(T);
 }
-constexpr int kFactWarpsD = 1;   // FP64: one zone per block, six blocks per SM
+constexpr int kFactWarpsD = 2;   // FP64: two zones per block, four blocks per SM
 constexpr int kFactWarpsF = 2;   // FP32
 
 cudaError_t predict_init(cudaStream_t s) {

@@ -87,6 +87,36 @@ def recon_flops(D, N, gated_linear_fraction=0.0):
             "z": (nv * z_calls * per_call, nv * z_calls * per_div)}
 
 
+def _mass_gmode_flops(emax, D=3, N=3):
+    """mass row of G from the momentum's coefficients (awe_predict.cu::
+    mass_gmode, mass_gmode_direct), over the G-modes (a, b, c, e) with
+    a+b+c+e <= N-1, e <= emax: per direction the derivative's one or two
+    source modes (the coefficient of L_e: 2 FMA for e = 0, FMA + mul for
+    e = 1, mul for e = 2; an FMA into the direction's sum), then an FMA with
+    lambda_d."""
+    flops = 0
+    cmax = N - 1 if D == 3 else 0
+    for e in range(emax + 1):
+        for c in range(cmax + 1):
+            for b in range(N):
+                for a in range(N):
+                    if a + b + c + e > N - 1:
+                        continue
+                    for d in range(D):
+                        abc = [a, b, c]
+                        for k in range(2):
+                            ad = abc[d]
+                            if k == 1 and ad != 0:
+                                break
+                            src = list(abc)
+                            src[d] = ad + 1 if k == 0 else 3
+                            if sum(src) + e > N:
+                                continue
+                            flops += (4 if e == 0 else 3 if e == 1 else 1) + 2
+                        flops += 2
+    return flops
+
+
 def predictor_flops(D, N, picard):
     """flops and divs per box zone of the predictor kernel."""
     nv = D + 2
@@ -97,21 +127,25 @@ def predictor_flops(D, N, picard):
         fma += 4 * 5 * 20 + 16 * 5 * 10 + 64 * 5 * 4       # w at the spatial nodes
         flops = 2 * fma
         divs = 0
+        # P1, P2 and P3 project the momentum and energy rows (4 variables);
+        # the mass row comes from the momentum's coefficients (mass_gmode)
         if picard >= 1:
             flops += 64 * fn
             divs += 64 * fd
-            flops += 2 * (3 * 5 * 16 * 3 * 4 + 3 * 5 * 4 * 6 * 4)   # P1, P2 with e = 0
-            flops += 5 * 10 * 3 * 4 * 3                                # P3 (mul + FMA)
+            flops += 2 * (3 * 4 * 16 * 3 * 4 + 3 * 4 * 4 * 6 * 4)   # P1, P2 with e = 0
+            flops += 4 * 10 * 3 * 4 * 3                                # P3 (mul + FMA)
+            flops += _mass_gmode_flops(0)
         for _ in range(1, picard):
             flops += 2 * (5 * 4 * 15 + 5 * 4 * 4 * 10 + 5 * 16 * 4 * 6)   # E1, E2, E3
-            # nodes: q and the 12 distinct flux entries (the momentum flux is
-            # symmetric: 24 flops and a division) at 4 time points, then the
-            # time contraction over the 2 symmetric pairs (sum and difference:
-            # 24 adds, 36 FMA)
-            flops += 64 * (4 * (2 * 5 * 3 + 24) + 2 * (24 + 2 * 36))
+            # nodes: q and the 9 distinct momentum and energy flux entries
+            # (the momentum flux is symmetric: 24 flops and a division) at 4
+            # time points, then the time contraction over the 2 symmetric
+            # pairs (sum and difference: 18 adds, 27 FMA)
+            flops += 64 * (4 * (2 * 5 * 3 + 24) + 2 * (18 + 2 * 27))
             divs += 64 * 4 * fd
-            flops += 2 * (3 * 5 * 16 * 6 * 4 + 3 * 5 * 4 * 10 * 4)        # P1, P2
-            flops += 5 * 15 * 3 * 4 * 3                                     # P3
+            flops += 2 * (3 * 4 * 16 * 6 * 4 + 3 * 4 * 4 * 10 * 4)        # P1, P2
+            flops += 4 * 15 * 3 * 4 * 3                                     # P3
+            flops += _mass_gmode_flops(2)
         # face states (factorised): G integrated at the two face times
         # (5 x 2 x 15 FMA), then per (variable, direction, side) the normal axis,
         # the two transverse axes and the time points: 124 FMA + 8 adds
@@ -126,8 +160,11 @@ def predictor_flops(D, N, picard):
     nq = (N + 2) // 2
     NFQ = nq ** D
     flops = divs = 0
+    # the node fluxes are projected for the momentum and energy rows (nv - 1);
+    # the mass row comes from the momentum's coefficients (mass_gmode_direct)
     if picard >= 1:
-        flops += NSN * (2 * nv * NS + fn + D * nv * (1 + 2 * NG0))
+        flops += NSN * (2 * nv * NS + fn + D * (nv - 1) * (1 + 2 * NG0))
+        flops += _mass_gmode_flops(0, D, N)
         divs += NSN * fd
     npair, nmid = NN // 2, NN % 2
     for _ in range(1, picard):
@@ -136,7 +173,8 @@ def predictor_flops(D, N, picard):
         # time contraction: a symmetric pair of time nodes enters through the
         # sum and the difference of its scaled fluxes (2 adds, 2 mul, NG FMA
         # per flux entry), the middle node of an odd rule alone (1 mul, NG FMA)
-        flops += NSN * D * nv * (npair * (4 + 2 * NG) + nmid * (1 + 2 * NG))
+        flops += NSN * D * (nv - 1) * (npair * (4 + 2 * NG) + nmid * (1 + 2 * NG))
+        flops += _mass_gmode_flops(N - 1, D, N)
         divs += NSN * NN * fd
     flops += D * 2 * NFQ * nv * 2 * (NS + NG)
     return flops, divs
