@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--order", type=int, default=4, choices=[2, 3, 4],
+                    help="order of the TGV workload (4: the headline; 2, 3 for profiling)")
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic form of the headline line (fp64 is the workload's)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-bulk form line")
@@ -137,9 +139,9 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
-def workload(n):
+def workload(n, order=4):
     from paper_2211_13295_gb300 import problems as P
-    return P.tgv3d(n=n, order=4, cfl=0.3)
+    return P.tgv3d(n=n, order=order, cfl=0.3)
 
 
 def workload_name(prob):
@@ -401,7 +403,7 @@ def run_native(args, rank, world, local):
     from paper_2211_13295_gb300 import awe, build, opcount
     build.build()
     torch.cuda.set_device(local)
-    prob = workload(args.n)
+    prob = workload(args.n, args.order)
     Uh = gpu_state(prob)
     grid = awe.Grid(prob, prec=args.form, gate=args.gate)
     if args.gate:
@@ -429,7 +431,7 @@ def run_native(args, rank, world, local):
     achieved = flops_pred / (avg_pred * 1e-3) / 1e12
     traffic = None
     tr_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_file):
+    if os.path.exists(tr_file) and prob.order == 4 and args.form == "fp64":
         traffic = json.load(open(tr_file)).get("predictor_fp64_per_launch")
     launches_per_step = sum(v[0] for v in prof.values()) / max(args.steps, 1)
     # kernel launches of the timed region: profiled spans + 1 finalize per step
@@ -519,7 +521,8 @@ def run_native(args, rank, world, local):
                        "l1_vs_oracle_one_step": parity},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"predictor (k_predict_fact<{'double' if args.form == 'fp64' else 'float'}>)",
+                         "kernel": f"predictor ({'k_predict_fact' if prob.order == 4 else 'k_predict_direct'}"
+                                   f"<{'double' if args.form == 'fp64' else 'float'}>)",
                          "peak_source": f"derived: 152 SMs x {'2 FP64' if args.form == 'fp64' else '128 FP32'} FMA/clk x 2 x 2.07 GHz",
                          "algorithmic_flops_per_launch": flops_pred, "avg_launch_ms": avg_pred,
                          "hbm": hbm_line},
@@ -541,13 +544,13 @@ def run_native(args, rank, world, local):
 
 def run_reference(args, rank, world):
     """The FP64 oracle as the reference arm: each step is one oracle step of the
-    same workload on a bounded sample (a periodic 24^3 Taylor-Green grid,
-    order 4, FP64, HLLC), on the host cores."""
+    same workload on a bounded sample (a periodic 24^3 Taylor-Green grid of
+    the workload's order, FP64, HLLC), on the host cores."""
     if rank != 0:
         return
     import oracle
     from paper_2211_13295_gb300 import problems as P
-    small = P.tgv3d(n=24, order=4, cfl=0.3)
+    small = P.tgv3d(n=24, order=args.order, cfl=0.3)
     U = small.initial_state()
     orc = oracle.Oracle(small)
     dt = orc.cfl_dt(U, small.cfl)
@@ -569,7 +572,8 @@ def run_reference(args, rank, world):
         "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(workload(args.n)), "sample": "tgv3d 24^3 order 4 per step"},
+        "config": {"workload": workload_name(workload(args.n, args.order)),
+                   "sample": f"tgv3d 24^3 order {args.order} per step"},
         "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "tgv3d 24^3 order 4 FP64, one oracle step per bench step"},
         "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

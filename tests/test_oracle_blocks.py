@@ -339,6 +339,70 @@ def test_predictor_advects_an_isolated_contact_exactly(dim, order):
     assert max(errs) > 1e-9
 
 
+def eval_dP(a, x):
+    """derivative of the scaled Legendre basis function P_a (closed form)"""
+    return sum(float(c) * j * x ** (j - 1) for j, c in P_MONO[a].items() if j > 0)
+
+
+def eval_st_ddx(coef, modes, xi, tau, d):
+    """d/dxi_d of a space-time polynomial given by its modal coefficients"""
+    acc = 0.0
+    for cf, (a, b, c, e) in zip(coef, modes):
+        f = [eval_P(a, xi[0]), eval_P(b, xi[1]), eval_P(c, xi[2])]
+        f[d] = eval_dP((a, b, c)[d], xi[d])
+        acc += cf * f[0] * f[1] * f[2] * shifted_L(e, tau)
+    return acc
+
+
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3), (3, 4)])
+def test_picard_mass_row_is_the_exact_momentum_divergence(dim, order):
+    """The mass flux of direction d is the momentum q_{1+d}, which lies in the
+    space the predictor projects onto (total degree <= N in space and time); the
+    (N+1)-point Gauss rules integrate its products with the test functions
+    exactly, so each Picard sweep must give, for a general (non-linear) state,
+    rho^{k+1}(xi, tau) = w_rho(xi) - sum_d lam_d int_0^tau d/dxi_d q^k_{1+d}(xi, s) ds
+    exactly: the space-time update of the method (the paper's predictor, Fig. 4)
+    for the one conservation law with a linear flux.  The right side is evaluated
+    here from the basis closed forms and a Gauss rule on [0, tau]."""
+    from paper_2211_13295_gb300 import problems as P
+    N = order - 1
+    prob = P.uniform(dim=dim, n=4, order=order)
+    rng = np.random.default_rng(100 * dim + order)
+    sm = s_modes(dim, N)
+    stm = st_modes(dim, N)
+    w = 0.1 * rng.normal(size=(dim + 2, len(sm)))
+    w[0][0], w[-1][0] = 1.0, 2.5
+    for d in range(dim):
+        w[1 + d][0] = 0.5 * rng.normal()
+    dt = 0.2 * prob.dx(0)
+    lam = [dt / prob.dx(d) for d in range(dim)]
+    xg, wg = oracle.gauss_legendre(N + 1)
+
+    def w_rho(xi):
+        return sum(cf * eval_P(a, xi[0]) * eval_P(b, xi[1]) * eval_P(c, xi[2]) for cf, (a, b, c) in zip(w[0], sm))
+
+    prev = None
+    for K in range(1, N + 1):
+        st = oracle.Oracle(prob.replace(picard=K)).predict_zone(w, dt)
+        for _ in range(12):
+            xi = list(rng.uniform(-0.5, 0.5, size=dim)) + [0.0] * (3 - dim)
+            tau = rng.uniform(0, 1)
+            rhs = w_rho(xi)
+            for d in range(dim):
+                if prev is None:   # q^0 = w: time-independent
+                    div = sum(cf * (eval_dP(a, xi[0]) if d == 0 else eval_P(a, xi[0])) *
+                              (eval_dP(b, xi[1]) if d == 1 else eval_P(b, xi[1])) *
+                              (eval_dP(c, xi[2]) if d == 2 else eval_P(c, xi[2]))
+                              for cf, (a, b, c) in zip(w[1 + d], sm))
+                    rhs -= lam[d] * tau * div
+                else:
+                    integ = sum(wq * tau * eval_st_ddx(prev[1 + d], stm, xi, tau * (xq + 0.5), d)
+                                for xq, wq in zip(xg, wg))
+                    rhs -= lam[d] * integ
+            assert abs(eval_st(st[0], stm, xi, tau) - rhs) < 1e-13
+        prev = st
+
+
 def test_fig5_face_state_convention(golden):
     """The paper's O2 flux builds the x-face states from the zone mean (mode 1),
     the x-slope (mode 2) and the time mode (mode 5) as U1 +/- U2/2 + U5/2
