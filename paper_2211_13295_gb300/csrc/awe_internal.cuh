@@ -91,8 +91,7 @@ __device__ __forceinline__ T pressure_of(const T* U, T gm1) {
 
 // Physical fluxes of all D directions at one state (shared 1/rho and p).
 template <int D, typename T>
-__device__ __forceinline__ void phys_fluxes(const T* U, T gm1, T F[D][D + 2]) {
-  T irho = T(1) / U[0];
+__device__ __forceinline__ void phys_fluxes_irho(const T* U, T irho, T gm1, T F[D][D + 2]) {
   T v[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) v[d] = U[1 + d] * irho;
@@ -110,6 +109,18 @@ __device__ __forceinline__ void phys_fluxes(const T* U, T gm1, T F[D][D + 2]) {
     F[d][D + 1] = Ep * v[d];
   }
 }
+template <int D, typename T>
+__device__ __forceinline__ void phys_fluxes(const T* U, T gm1, T F[D][D + 2]) {
+  phys_fluxes_irho<D, T>(U, T(1) / U[0], gm1, F);
+}
+// 1/a and 1/b from one division: 1/a = b / (ab), 1/b = a / (ab) (densities of
+// a pair of nodes; ab stays far inside the range for physical densities)
+template <typename T>
+__device__ __forceinline__ void recip_pair(T a, T b, T& ia, T& ib) {
+  const T r = T(1) / (a * b);
+  ia = b * r;
+  ib = a * r;
+}
 
 // HLLC flux across a face normal to direction dir (Toro, Spruce & Speares):
 // Davis-Einfeldt wave speeds with Roe averages, S* from the pressure
@@ -118,7 +129,8 @@ template <int D, typename T>
 __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma, T* F) {
   const T gm1 = gamma - T(1);
   T rl = UL[0], rr = UR[0];
-  T irl = T(1) / rl, irr = T(1) / rr;
+  T irl, irr;
+  recip_pair<T>(rl, rr, irl, irr);
   T vl[D], vr[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -207,7 +219,8 @@ __device__ __forceinline__ void hll_family(const T* UL, const T* UR, int dir, T 
   constexpr int NV = D + 2;
   const T gm1 = gamma - T(1);
   T rl = UL[0], rr = UR[0];
-  T irl = T(1) / rl, irr = T(1) / rr;
+  T irl, irr;
+  recip_pair<T>(rl, rr, irl, irr);
   T vl[D], vr[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -277,7 +290,8 @@ template <int D, typename T>
 __device__ __forceinline__ void rusanov(const T* UL, const T* UR, int dir, T gamma, T* F) {
   constexpr int NV = D + 2;
   const T gm1 = gamma - T(1);
-  T irl = T(1) / UL[0], irr = T(1) / UR[0];
+  T irl, irr;
+  recip_pair<T>(UL[0], UR[0], irl, irr);
   T vl[D], vr[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {

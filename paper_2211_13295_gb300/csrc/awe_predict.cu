@@ -202,21 +202,27 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
           for (int t = 0; t < (NN + 1) / 2; ++t) {
             const int t2 = NN - 1 - t;
             T Fa[D][D + 2], Fb[D][D + 2];
+            T qn[2][NV];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               if (h == 1 && t2 == t) break;
               const int node = s * NN + (h ? t2 : t);
               const T* ev = EV + (long long)node * NG;
-              T qn[NV];
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
                 T acc = wn[v];
 #pragma unroll
                 for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], ev[b], acc);
-                qn[v] = acc;
+                qn[h][v] = acc;
               }
-              if (h) phys_fluxes<D, T>(qn, gm1, Fb);
-              else phys_fluxes<D, T>(qn, gm1, Fa);
+            }
+            if (t2 != t) {
+              T ia, ib;
+              recip_pair<T>(qn[0][0], qn[1][0], ia, ib);
+              phys_fluxes_irho<D, T>(qn[0], ia, gm1, Fa);
+              phys_fluxes_irho<D, T>(qn[1], ib, gm1, Fb);
+            } else {
+              phys_fluxes<D, T>(qn[0], gm1, Fa);
             }
 #pragma unroll
             for (int d = 0; d < D; ++d) {
@@ -547,8 +553,7 @@ template <typename T> struct NodeAcc {
 };
 
 template <typename T>
-__device__ __forceinline__ void sym_fluxes(const T* qn, T gm1, T* f) {
-  const T irho = T(1) / qn[0];
+__device__ __forceinline__ void sym_fluxes(const T* qn, T irho, T gm1, T* f) {
   T vel[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) vel[d] = qn[1 + d] * irho;
@@ -842,11 +847,10 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
           NodeAcc<T> acc = {};
 #pragma unroll
           for (int tp = 0; tp < 2; ++tp) {
-            T f[2][9];
+            T f[2][9], qn[2][5];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int t = h ? 3 - tp : tp;
-              T qn[5];
 #pragma unroll
               for (int v = 0; v < 5; ++v) {
                 T x = swn[v * 64 + s];
@@ -856,10 +860,13 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
                   const T cc = t == 0 ? q4.x : t == 1 ? q4.y : t == 2 ? q4.z : q4.w;
                   x = fma(-cc, pnk[c], x);
                 }
-                qn[v] = x;
+                qn[h][v] = x;
               }
-              sym_fluxes<T>(qn, gm1, f[h]);
             }
+            T ia, ib;
+            recip_pair<T>(qn[0][0], qn[1][0], ia, ib);
+            sym_fluxes<T>(qn[0], ia, gm1, f[0]);
+            sym_fluxes<T>(qn[1], ib, gm1, f[1]);
             accumulate_pair<T>(acc, f[0], f[1], tc, tp);
           }
           store_node_y1<T>(Y1, s, acc);
@@ -875,20 +882,22 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
         NodeAcc<T> acc = {};
 #pragma unroll
         for (int tp = 0; tp < 2; ++tp) {
-          T f[2][9];
+          T f[2][9], qn[2][5];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int t = h ? 3 - tp : tp;
-            T qn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
               T x = FactSmem<T>::WN_REG ? (hs ? wnr[1][v] : wnr[0][v]) : swn[v * 64 + s];
 #pragma unroll
               for (int c = 0; c < 3; ++c) x = fma(-C[((((v * 4 + i) * 4 + j) * 3 + c) * 4) + t], pnk[c], x);
-              qn[v] = x;
+              qn[h][v] = x;
             }
-            sym_fluxes<T>(qn, gm1, f[h]);
           }
+          T ia, ib;
+          recip_pair<T>(qn[0][0], qn[1][0], ia, ib);
+          sym_fluxes<T>(qn[0], ia, gm1, f[0]);
+          sym_fluxes<T>(qn[1], ib, gm1, f[1]);
           accumulate_pair<T>(acc, f[0], f[1], tc, tp);
         }
         store_node_y1<T>(Y1, s, acc);
