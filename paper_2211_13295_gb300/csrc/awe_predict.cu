@@ -298,8 +298,8 @@ template <typename T> struct FactSmem {
   static constexpr int WN = W + 100;                   // wn[5][64] (FP32)
   static constexpr int G = WN + (WN_REG ? 0 : 320);    // g[5][15]
   static constexpr int R1 = WN_REG ? G + 75 : G + 76;  // (FP32: 16-byte aligned C rows)
-  static constexpr int R2 = R1 + 960;                  // A/B, Y1 (2304)
-  static constexpr int SIZE = R2 + 2304;               // 3439 (FP64), 3760 (FP32)
+  static constexpr int R2 = R1 + 960;                  // A/B, Y1 (1728), Y3
+  static constexpr int SIZE = R2 + 1728;               // 2863 (FP64), 3184 (FP32)
 };
 
 // index tables copied to shared memory once per block (lane-divergent reads
@@ -312,6 +312,10 @@ struct FactIdx {
   // (offsets into the w / g rows, 255 = none), [4] w of the mode three degrees
   // up (b = 0 only), [5] the derivative factor of the first (1, 2 or 3)
   uint8_t mass_src[3][6][16];
+  // projection (fact_project): first axis of each of the 9 flux row sets; per
+  // (d, v') its row set, whether d is the lower of the two axes P1 leaves, and
+  // whether the P2 axis is above the P1 axis (transverse modes swapped in Y3)
+  int8_t p1c1[9], p2row[12], p2lo[12], p2swap[12];
 };
 __constant__ FactIdx c_fidx;
 
@@ -404,119 +408,116 @@ __device__ __forceinline__ T mass_gmode(const T* z, const FactIdx& ix, int b, co
 }
 
 // Picard projection of the node fluxes of the momentum and energy rows (the
-// mass row by mass_gmode).  Y1 rows v' = 0..3 hold the variables 1..4.
+// mass row by mass_gmode).  Y1 holds the 9 distinct flux entries ("row sets")
+// r at the nodes: 0..2 the diagonal momentum flux of direction r, 3..5 the
+// off-diagonal momentum flux rho v_a v_b of the pairs (0,1), (0,2), (1,2),
+// 6..8 the energy flux of direction r - 6.  Direction d's flux of the variable
+// 1 + v' (v' = 0..3) is projected with the plain basis along the two axes
+// other than d (P1, P2) and with the derivative factors along d (P3).  P1 takes
+// the axis c1(r) first: for an off-diagonal entry the axis that is neither of
+// its two directions, so that one P1 serves both; P2 then contracts the
+// remaining axis c2 of each (d, v'), and Y3 keeps the canonical order of the
+// two transverse modes (lower axis first).
 template <typename T, int EMAX>
 __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const FactIdx& ix, int lane,
                                              const T lam[3]) {
   constexpr int NPE = EMAX == 0 ? 3 : 6;     // (p,e) pairs with e <= EMAX
   constexpr int NTR = EMAX == 0 ? 6 : 10;    // (p,q,e) triples with e <= EMAX
   constexpr int NGE = EMAX == 0 ? 10 : 15;   // G-modes with e <= EMAX
-  const T* Y1 = z + FactSmem<T>::R2;         // [d][v'][s][e3]  (e3 stride 3)
-  T* Y2 = z + FactSmem<T>::R1;               // [v'][n2][pe]    one direction (pe stride 6)
-  T* Y3 = z + FactSmem<T>::R1 + 384;         // [d][v'][n1][tri] (tri stride 10)
+  const T* Y1 = z + FactSmem<T>::R2;         // [r][s][e3]          (e3 stride 3)
+  T* Y2 = z + FactSmem<T>::R1;               // [r][n2][pe]         (pe stride 6)
+  T* Y3 = z + FactSmem<T>::R2;               // [d][v'][n1][tri]    (tri stride 10; Y1 is dead)
   // the mass row from the previous G, before P3 overwrites it
   const T gmass = lane < NGE ? mass_gmode<T>(z, ix, lane, lam) : T(0);
-  // one direction at a time: P1 contracts the first dimension (z for d = x,
-  // y; y for d = z), P2 the second (y for d = x; x for d = y, z).  Static lane
-  // mappings (kStatic): P1 lanes own (n2, half of the (p,e) pairs), P2 lanes
-  // own (n1, v); the remaining indices are compile-time loops, so the basis
-  // values are uniform constant-bank operands.
+  // Static lane mappings (kStatic): P1 lanes own (n2, a group of row sets),
+  // P2 lanes own (n1, d, v'); the remaining indices are compile-time loops, so
+  // the basis values are uniform constant-bank operands.
   const Tabs<T>& tc = tabs<T>(3);
+  if constexpr ((kStatic<T> & kStP1) != 0) {
+    // lanes own (n2, row sets 0-4 or 5-8) and compute every (p,e) pair of a
+    // row set from its 4 x (EMAX+1) values, loaded once
+    const int n2 = lane & 15, vh = lane >> 4;
+    const int a0 = n2 & 3, a1 = n2 >> 2;
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    if constexpr ((kStatic<T> & kStP1) != 0) {
-      {
-        // lanes own (n2, a pair of rows: 0-1 or 2-3) and compute every (p,e)
-        // pair of a row from its 4 x (EMAX+1) values, loaded once
-        const int n2 = lane & 15, vh = lane >> 4;
-        const int a0 = n2 & 3, a1 = n2 >> 2;
-        const int sbase = d < 2 ? (a0 + 4 * a1) : (a0 + 16 * a1);
-        const int sstr = d < 2 ? 16 : 4;
-        const T* y1 = Y1 + (d * 4) * 64 * 3;
-#pragma unroll 1
-        for (int v = 2 * vh; v < 2 * vh + 2; ++v) {
-          const T* yv = y1 + v * 64 * 3 + sbase * 3;
-          T y[EMAX + 1][4];
+    for (int r = vh ? 5 : 0; r < (vh ? 9 : 5); ++r) {
+      const int c1 = ix.p1c1[r];
+      const int str = 3 << (2 * c1);
+      const int base = c1 == 0 ? 4 * a0 + 16 * a1 : c1 == 1 ? a0 + 16 * a1 : a0 + 4 * a1;
+      const T* yv = Y1 + (r * 64 + base) * 3;
+      T y[EMAX + 1][4];
 #pragma unroll
-          for (int m = 0; m < 4; ++m)
+      for (int m = 0; m < 4; ++m)
 #pragma unroll
-            for (int e = 0; e <= EMAX; ++e) y[e][m] = yv[m * sstr * 3 + e];
+        for (int e = 0; e <= EMAX; ++e) y[e][m] = yv[m * str + e];
 #pragma unroll
-          for (int pe = 0; pe < NPE; ++pe) {
-            const int p = pair2_p(pe), e = pair2_e(pe);
-            T acc = T(0);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) acc = fma(y[e][m], tc.WPN[p][m], acc);
-            Y2[(v * 16 + n2) * 6 + pe] = acc;
-          }
-        }
-      }
-    } else {
-#pragma unroll 2
-      for (int it = lane; it < 4 * 16 * NPE; it += 32) {
-        int pe = it % NPE;
-        int rest = it / NPE;
-        int n2 = rest % 16;
-        int v = rest / 16;
-        int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
-        int a0 = n2 & 3, a1 = n2 >> 2;
+      for (int pe = 0; pe < NPE; ++pe) {
+        const int p = pair2_p(pe), e = pair2_e(pe);
         T acc = T(0);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          // d < 2: n2 = (i,j), sum over k; d = 2: n2 = (i,k), sum over j
-          int s = d < 2 ? (a0 + 4 * a1 + 16 * m) : (a0 + 4 * m + 16 * a1);
-          acc = fma(Y1[((d * 4 + v) * 64 + s) * 3 + e], tb.WPN[p][m], acc);
-        }
-        Y2[(v * 16 + n2) * 6 + pe] = acc;
+        for (int m = 0; m < 4; ++m) acc = fma(y[e][m], tc.WPN[p][m], acc);
+        Y2[(r * 16 + n2) * 6 + pe] = acc;
       }
     }
-    __syncwarp();
-    if constexpr ((kStatic<T> & kStP2) != 0) {
-      if (lane < 16) {
-        const int n1 = lane & 3, v = lane >> 2;
-        const int nbase = d == 0 ? n1 : 4 * n1;
-        const int nstr = d == 0 ? 4 : 1;
-        const T* y2 = Y2 + v * 16 * 6;
-        T y[NPE][4];  // every operand once
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-#pragma unroll
-          for (int pe = 0; pe < NPE; ++pe) y[pe][m] = y2[(nbase + m * nstr) * 6 + pe];
-#pragma unroll
-        for (int pe = 0; pe < NPE; ++pe) {
-          const int qq = pair2_p(pe), e = pair2_e(pe);
-#pragma unroll
-          for (int p = 0; p <= 2 - qq - e; ++p) {
-            T acc = T(0);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) acc = fma(y[pe][m], tc.WPN[p][m], acc);
-            Y3[((d * 4 + v) * 4 + n1) * 10 + tri2idx(p, qq, e)] = acc;
-          }
-        }
-      }
-    } else {
+  } else {
 #pragma unroll 2
-      for (int it = lane; it < 4 * 4 * NTR; it += 32) {
-        int tr = it % NTR;
-        int rest = it / NTR;
-        int n1 = rest % 4;
-        int v = rest / 4;
-        int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
-        // d = x: Y3[i][(b,c,e)] = sum_j Y2[(i,j)][(c,e)] WPN[b][j]      (p=b, qq=c)
-        // d = y: Y3[j][(a,c,e)] = sum_i Y2[(i,j)][(c,e)] WPN[a][i]      (p=a, qq=c)
-        // d = z: Y3[k][(a,b,e)] = sum_i Y2[(i,k)][(b,e)] WPN[a][i]      (p=a, qq=b)
-        int pe = ix.pair2_idx[qq][e];
-        T acc = T(0);
+    for (int it = lane; it < 9 * 16 * NPE; it += 32) {
+      const int pe = it % NPE, rest = it / NPE, n2 = rest % 16, r = rest / 16;
+      const int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
+      const int c1 = ix.p1c1[r];
+      const int a0 = n2 & 3, a1 = n2 >> 2;
+      const int str = 3 << (2 * c1);
+      const int base = c1 == 0 ? 4 * a0 + 16 * a1 : c1 == 1 ? a0 + 16 * a1 : a0 + 4 * a1;
+      const T* yv = Y1 + (r * 64 + base) * 3 + e;
+      T acc = T(0);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          int n2 = d == 0 ? (n1 + 4 * m) : (m + 4 * n1);
-          acc = fma(Y2[(v * 16 + n2) * 6 + pe], tb.WPN[p][m], acc);
-        }
-        Y3[((d * 4 + v) * 4 + n1) * 10 + tr] = acc;
-      }
+      for (int m = 0; m < 4; ++m) acc = fma(yv[m * str], tb.WPN[p][m], acc);
+      Y2[(r * 16 + n2) * 6 + pe] = acc;
     }
-    __syncwarp();
   }
+  __syncwarp();
+  if constexpr ((kStatic<T> & kStP2) != 0) {
+    // lanes own (n1, d, v'): 48 items in two rounds
+#pragma unroll 1
+    for (int it = lane; it < 48; it += 32) {
+      const int n1 = it & 3, dv = it >> 2;
+      const int r = ix.p2row[dv];
+      const bool lo = ix.p2lo[dv] != 0, swap = ix.p2swap[dv] != 0;
+      const int nbase = lo ? n1 : 4 * n1, nstr = lo ? 4 : 1;
+      const T* y2 = Y2 + r * 16 * 6;
+      T y[NPE][4];  // every operand once
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int pe = 0; pe < NPE; ++pe) y[pe][m] = y2[(nbase + m * nstr) * 6 + pe];
+#pragma unroll
+      for (int pe = 0; pe < NPE; ++pe) {
+        const int qq = pair2_p(pe), e = pair2_e(pe);
+#pragma unroll
+        for (int p = 0; p <= 2 - qq - e; ++p) {
+          T acc = T(0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) acc = fma(y[pe][m], tc.WPN[p][m], acc);
+          Y3[(dv * 4 + n1) * 10 + (swap ? tri2idx(qq, p, e) : tri2idx(p, qq, e))] = acc;
+        }
+      }
+    }
+  } else {
+#pragma unroll 2
+    for (int it = lane; it < 12 * 4 * NTR; it += 32) {
+      // tr = (p, qq, e): p the mode along c2 (this step), qq along c1 (P1)
+      const int tr = it % NTR, rest = it / NTR, n1 = rest % 4, dv = rest / 4;
+      const int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
+      const int r = ix.p2row[dv];
+      const int pe = ix.pair2_idx[qq][e];
+      const bool lo = ix.p2lo[dv] != 0;
+      const T* y2 = Y2 + r * 16 * 6 + pe;
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc = fma(y2[(lo ? n1 + 4 * m : m + 4 * n1) * 6], tb.WPN[p][m], acc);
+      Y3[(dv * 4 + n1) * 10 + (ix.p2swap[dv] ? ix.tri_idx[qq][p][e] : tr)] = acc;
+    }
+  }
+  __syncwarp();
   // P3: contract the derivative dimension with the Q factors, sum over d
   for (int it = lane; it < 4 * NGE; it += 32) {
     int b = it % NGE;
@@ -584,21 +585,13 @@ __device__ __forceinline__ void accumulate_pair(NodeAcc<T>& acc, const T* fa, co
   }
 }
 
-// Y1[d][v'][s][e] for the variables 1 + v': v' = d diagonal momentum, v' = c
-// (c != d) the off-diagonal entry of the pair (d, c) (entry 3 + d + c - 1),
-// v' = 3 energy
+// Y1[r][s][e]: the 9 distinct entries in NodeAcc order (fact_project)
 template <typename T>
 __device__ __forceinline__ void store_node_y1(T* Y1, int s, const NodeAcc<T>& acc) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d)
+  for (int r = 0; r < 9; ++r)
 #pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      Y1[((d * 4 + 3) * 64 + s) * 3 + e] = acc.a[6 + d][e];
-      Y1[((d * 4 + d) * 64 + s) * 3 + e] = acc.a[d][e];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c != d) Y1[((d * 4 + c) * 64 + s) * 3 + e] = acc.a[3 + d + c - 1][e];
-    }
+    for (int e = 0; e < 3; ++e) Y1[(r * 64 + s) * 3 + e] = acc.a[r][e];
 }
 
 template <typename T, int WPB>
@@ -726,9 +719,13 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
         for (int v = 0; v < 5; ++v) qn[v] = FactSmem<T>::WN_REG ? wnr[hs][v] : swn[v * 64 + s];
         phys_fluxes<3, T>(qn, gm1, F);
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-          for (int v = 1; v < 5; ++v) Y1[((d * 4 + v - 1) * 64 + s) * 3 + 0] = F[d][v];
+        for (int d = 0; d < 3; ++d) {
+          Y1[(d * 64 + s) * 3] = F[d][1 + d];          // diagonal momentum
+          Y1[((6 + d) * 64 + s) * 3] = F[d][4];        // energy
+        }
+        Y1[(3 * 64 + s) * 3] = F[0][2];                // rho v_x v_y
+        Y1[(4 * 64 + s) * 3] = F[0][3];                // rho v_x v_z
+        Y1[(5 * 64 + s) * 3] = F[1][3];                // rho v_y v_z
       }
       __syncwarp();
       fact_project<T, 0>(z, tb, ix, lane, lam);
@@ -1073,6 +1070,20 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
       }
     }
   }
+  // projection axes (fact_project)
+  const int c1tab[9] = {2, 2, 1, 2, 1, 0, 2, 2, 1};
+  for (int r = 0; r < 9; ++r) h.p1c1[r] = (int8_t)c1tab[r];
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < 4; ++v) {
+      const int lo_ = v < d ? v : d, hi_ = v < d ? d : v;
+      const int r = v == 3 ? 6 + d : v == d ? d : 3 + lo_ + hi_ - 1;
+      const int c1 = c1tab[r];
+      const int alo = c1 == 0 ? 1 : 0, ahi = c1 == 2 ? 1 : 2;   // the two axes other than c1
+      const int c2 = d == alo ? ahi : alo;
+      h.p2row[d * 4 + v] = (int8_t)r;
+      h.p2lo[d * 4 + v] = (int8_t)(d == alo);
+      h.p2swap[d * 4 + v] = (int8_t)(c2 > c1);
+    }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_fidx, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;

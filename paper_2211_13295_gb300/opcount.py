@@ -128,11 +128,13 @@ def predictor_flops(D, N, picard):
         flops = 2 * fma
         divs = 0
         # P1, P2 and P3 project the momentum and energy rows (4 variables);
-        # the mass row comes from the momentum's coefficients (mass_gmode)
+        # the mass row comes from the momentum's coefficients (mass_gmode).
+        # P1 runs once per distinct flux entry (9 row sets: the off-diagonal
+        # momentum flux serves two directions), P2 per (direction, variable)
         if picard >= 1:
             flops += 64 * fn
             divs += 64 * fd
-            flops += 2 * (3 * 4 * 16 * 3 * 4 + 3 * 4 * 4 * 6 * 4)   # P1, P2 with e = 0
+            flops += 2 * (9 * 16 * 3 * 4 + 12 * 4 * 6 * 4)         # P1, P2 with e = 0
             flops += 4 * 10 * 3 * 4 * 3                                # P3 (mul + FMA)
             flops += _mass_gmode_flops(0)
         for _ in range(1, picard):
@@ -143,7 +145,7 @@ def predictor_flops(D, N, picard):
             # pairs (sum and difference: 18 adds, 27 FMA)
             flops += 64 * (4 * (2 * 5 * 3 + 24) + 2 * (18 + 2 * 27))
             divs += 64 * 4 * fd
-            flops += 2 * (3 * 4 * 16 * 6 * 4 + 3 * 4 * 4 * 10 * 4)        # P1, P2
+            flops += 2 * (9 * 16 * 6 * 4 + 12 * 4 * 10 * 4)               # P1, P2
             flops += 4 * 15 * 3 * 4 * 3                                     # P3
             flops += _mass_gmode_flops(2)
         # face states (factorised): G integrated at the two face times
