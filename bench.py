@@ -197,6 +197,37 @@ def time_e2e(grid, Uh, steps, world):
     return (time.perf_counter() - t0) * 1e3
 
 
+def cpu_model():
+    """the host CPU's model name (lscpu), else the architecture"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_one_core(order):
+    """The oracle on one host core (OpenMP limited to one thread in a child
+    process): one step of a periodic 16^3 Taylor-Green grid."""
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle; "
+            "from paper_2211_13295_gb300 import problems as P; "
+            "p = P.tgv3d(n=16, order=%d, cfl=0.3); U = p.initial_state(); o = oracle.Oracle(p); "
+            "dt = o.cfl_dt(U, p.cfl); t0 = time.perf_counter(); o.step(U, 0.0, dt); "
+            "print(p.zones / (time.perf_counter() - t0))") % (ROOT, order)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        v = float(out.stdout.strip().splitlines()[-1])
+    except Exception as e:
+        return {"value": None, "error": str(e)[:200]}
+    return {"value": v, "unit": "zone-updates/s", "cores": 1,
+            "sample": f"one step of tgv3d 16^3 order {order} FP64 (4096 zones), OMP_NUM_THREADS=1"}
+
+
 def cpu_baseline_and_parity(prob, grid_state_after, U0, dt0, n_windows=3, m=4, seed=0):
     """The FP64 oracle (a) timed on a bounded sample of the workload (a full
     periodic 32^3 Taylor-Green grid, one step, all host cores) and (b) run on
@@ -212,7 +243,8 @@ def cpu_baseline_and_parity(prob, grid_state_after, U0, dt0, n_windows=3, m=4, s
     orc.step(Us, 0.0, dts)
     el = time.perf_counter() - t0
     base = {"value": small.zones / el, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
-            "sample": f"one step of tgv3d 32^3 order {prob.order} FP64 (32768 zones), {el:.1f} s wall"}
+            "sample": f"one step of tgv3d 32^3 order {prob.order} FP64 (32768 zones), {el:.1f} s wall",
+            "cpu_model": cpu_model(), "one_core": oracle_one_core(prob.order)}
     # parity on windows of the full-size first step
     parity = None
     if grid_state_after is not None:
