@@ -135,10 +135,14 @@ int awe_destroy(awe_grid* g);
 const char* awe_last_error(const awe_grid* g);
 
 /* Copy a state in (on_device = 0: host pointer, 1: device pointer on this
- * GPU) in the state layout above.  Fig. 1 "update device(U_skinny)". */
+ * GPU) in the state layout above.  Fig. 1 "update device(U_skinny)".  A
+ * page-locked host buffer (cudaHostAlloc / cudaHostRegister) is read directly
+ * by the library's scatter kernel; pageable memory is staged through device
+ * memory with a copy.  Synchronises when on_device = 0. */
 int awe_set_state(awe_grid* g, const double* U, int on_device);
 /* Copy the state out (host or device pointer, caller owned).  Fig. 1
- * "update host(U_skinny)".  Synchronises when on_device = 0. */
+ * "update host(U_skinny)".  A page-locked host buffer is written directly by
+ * the gather kernel.  Synchronises when on_device = 0. */
 int awe_get_state(awe_grid* g, double* U, int on_device);
 /* Simulation time t (start of the next step; used by time-dependent BCs). */
 int awe_set_time(awe_grid* g, double t);

@@ -587,12 +587,27 @@ int awe_destroy(awe_grid* g) {
   return AWE_OK;
 }
 
+// A page-locked host buffer that the device addresses at the same virtual
+// address (unified addressing): the scatter / gather kernels then read or
+// write it directly over the host link.  That skips the copy engine, whose
+// first transfer after an idle period of about a second costs tens of
+// milliseconds on this platform.  Anything else (pageable memory) goes through
+// the staging buffer with cudaMemcpyAsync.
+static bool host_mapped(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 int awe_set_state(awe_grid* g, const double* U, int on_device) {
   if (!g || !U) return fail(g, AWE_ERR_ARG, "null argument");
   const Geo& q = g->q;
   long long n = nactive(q) * q.nv;
   const double* src = U;
-  if (!on_device) {
+  if (!on_device && !host_mapped(U)) {
     CK(g, cudaMemcpyAsync(g->stage, U, sizeof(double) * n, cudaMemcpyHostToDevice, g->s));
     src = g->stage;
   }
@@ -607,12 +622,13 @@ int awe_get_state(awe_grid* g, double* U, int on_device) {
   if (!g || !U) return fail(g, AWE_ERR_ARG, "null argument");
   const Geo& q = g->q;
   long long n = nactive(q) * q.nv;
-  double* dst = on_device ? U : g->stage;
+  const bool mapped = !on_device && host_mapped(U);
+  double* dst = on_device || mapped ? U : g->stage;
   int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
   k_gather<<<blocks, 256, 0, g->s>>>(q, g->U[g->cur], dst);
   CK(g, cudaGetLastError());
   if (!on_device) {
-    CK(g, cudaMemcpyAsync(U, g->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, g->s));
+    if (!mapped) CK(g, cudaMemcpyAsync(U, g->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, g->s));
     CK(g, cudaStreamSynchronize(g->s));
   }
   return AWE_OK;

@@ -246,42 +246,62 @@ __global__ void __launch_bounds__(128) k_predict_direct(Geo q, Region box, const
     // face quadrature states: q = w(face point) - int_0^tau G; with the
     // positivity fallback, a first pass checks every face point and a zone
     // with a non-physical one writes its mean instead
+    // Rows (d, side, point) with point = sp + NSP * it: the w part depends on
+    // the spatial point sp only, so it is formed once for the NQ time points.
+    constexpr int NSP = NFQ / M::NQ;   // spatial points per face
     bool bad = false;
     if (q.fallback) {
-      for (int row = 0; row < D * 2 * NFQ; ++row) {
-        const T* fw = FW + (long long)row * NS;
-        const T* fg = FG + (long long)row * NG;
-        T u[NV];
+      for (int ds = 0; ds < D * 2; ++ds)
+        for (int sp = 0; sp < NSP; ++sp) {
+          const T* fw = FW + (long long)(ds * NFQ + sp) * NS;
+          T wv[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m < NS; ++m) acc = fma(w[v][m], fw[m], acc);
+            wv[v] = acc;
+          }
+#pragma unroll
+          for (int it = 0; it < M::NQ; ++it) {
+            const T* fg = FG + (long long)(ds * NFQ + sp + NSP * it) * NG;
+            T u[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              T acc = wv[v];
+#pragma unroll
+              for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
+              u[v] = acc;
+            }
+            bad = bad || !state_physical<D, T>(u, gm1);
+          }
+        }
+      if (bad && q.fb_count) atomicAdd(q.fb_count, 1ULL);
+    }
+    for (int ds = 0; ds < D * 2; ++ds)
+      for (int sp = 0; sp < NSP; ++sp) {
+        const T* fw = FW + (long long)(ds * NFQ + sp) * NS;
+        T wv[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           T acc = T(0);
 #pragma unroll
           for (int m = 0; m < NS; ++m) acc = fma(w[v][m], fw[m], acc);
-#pragma unroll
-          for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
-          u[v] = acc;
+          wv[v] = acc;
         }
-        bad = bad || !state_physical<D, T>(u, gm1);
-      }
-      if (bad && q.fb_count) atomicAdd(q.fb_count, 1ULL);
-    }
-    for (int row = 0; row < D * 2 * NFQ; ++row) {
-      const T* fw = FW + (long long)row * NS;
-      const T* fg = FG + (long long)row * NG;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        T acc = T(0);
-        if (bad) {
-          acc = w[v][0];
-        } else {
+        for (int it = 0; it < M::NQ; ++it) {
+          const int row = ds * NFQ + sp + NSP * it;
+          const T* fg = FG + (long long)row * NG;
 #pragma unroll
-          for (int m = 0; m < NS; ++m) acc = fma(w[v][m], fw[m], acc);
+          for (int v = 0; v < NV; ++v) {
+            T acc = wv[v];
 #pragma unroll
-          for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
+            for (int b = 0; b < NG; ++b) acc = fma(-g[v][b], fg[b], acc);
+            FS[((long long)row * NV + v) * nb + r] = bad ? w[v][0] : acc;
+          }
         }
-        FS[((long long)row * NV + v) * nb + r] = acc;
       }
-    }
   }
 }
 

@@ -178,7 +178,9 @@ def predictor_flops(D, N, picard):
         flops += NSN * D * (nv - 1) * (npair * (4 + 2 * NG) + nmid * (1 + 2 * NG))
         flops += _mass_gmode_flops(N - 1, D, N)
         divs += NSN * NN * fd
-    flops += D * 2 * NFQ * nv * 2 * (NS + NG)
+    # face states: the w part once per spatial face point, the G part per
+    # space-time point
+    flops += D * 2 * (NFQ // nq) * nv * 2 * NS + D * 2 * NFQ * nv * 2 * NG
     return flops, divs
 
 
