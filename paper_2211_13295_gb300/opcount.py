@@ -81,7 +81,9 @@ def recon_flops(D, N, gated_linear_fraction=0.0):
     # calls per zone and variable in each pass
     x_calls = 1
     y_calls = 1 + (N - 1)                       # recon_y(U), recon_y(X[a]) a < N
-    z_calls = 0 if D == 2 else 1 + 2 * (N - 1) + N * (N - 1) // 2 - (1 if N == 3 else 0)
+    # recon_z(U), recon_z(X[a]) and recon_z(Y[a]) for a < N, recon_z(XY[a][b])
+    # for a, b >= 1 with a + b < N
+    z_calls = 0 if D == 2 else 1 + 2 * (N - 1) + (N - 1) * (N - 2) // 2
     return {"x": (nv * x_calls * per_call, nv * x_calls * per_div),
             "y": (nv * y_calls * per_call, nv * y_calls * per_div),
             "z": (nv * z_calls * per_call, nv * z_calls * per_div)}
