@@ -614,8 +614,11 @@ __device__ __forceinline__ void store_node_y1(T* Y1, int s, const NodeAcc<T>& ac
     for (int e = 0; e < 3; ++e) Y1[(r * 64 + s) * 3 + e] = acc.a[r][e];
 }
 
+// Register budgets: FP32 at 8 blocks of two zone-warps per SM (its shared
+// memory allows 8); FP64 at most ~170 registers (its shared memory allows 4
+// blocks; more registers measured slower)
 template <typename T, int WPB>
-__global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, const T* __restrict__ W,
+__global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fact(Geo q, Region box, const T* __restrict__ W,
                                                            const double* __restrict__ d_dt, int picard,
                                                            const T* __restrict__ tab, PTabLayout L,
                                                            T* __restrict__ FS) {
@@ -939,57 +942,60 @@ __global__ void __launch_bounds__(32 * WPB) k_predict_fact(Geo q, Region box, co
     __syncwarp();
     if (lane < 30) {
       const int v = lane % 5, ds = lane / 5, d = ds >> 1, side = ds & 1;
-      // axes: n = d (normal), t1 < t2 the transverse ones
-      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      // axes: n = d (normal), t1 < t2 the transverse ones.  Every loop below
+      // is unrolled over compile-time exponents; the mode index of (an on the
+      // normal axis, p1 on t1, p2 on t2) is one of three constants, picked by d
       // w part: contract the normal axis at the face, then t1, then t2
-      T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index pair3_idx[p1][p2]
-#pragma unroll 1
-      for (int pc = 0; pc < 10; ++pc) {
-        int p1 = ix.pair3[pc][0], p2 = ix.pair3[pc][1];
-        T acc = T(0);
-        for (int an = 0; an <= 3 - p1 - p2; ++an) {
-          int abc[3];
-          abc[d] = an;
-          abc[t1] = p1;
-          abc[t2] = p2;
-          acc = fma(sw[v * 20 + ix.sm3_idx[abc[0]][abc[1]][abc[2]]], tb.PE[an][side], acc);
+      T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index p3idx(p1, p2)
+#pragma unroll
+      for (int p2 = 0; p2 <= 3; ++p2)
+#pragma unroll
+        for (int p1 = 0; p1 <= 3 - p2; ++p1) {
+          T acc = T(0);
+#pragma unroll
+          for (int an = 0; an <= 3 - p1 - p2; ++an) {
+            const int m = d == 0 ? simplex_idx(3, an, p1, p2) : d == 1 ? simplex_idx(3, p1, an, p2)
+                                                                      : simplex_idx(3, p1, p2, an);
+            acc = fma(sw[v * 20 + m], tb.PE[an][side], acc);
+          }
+          wn2[p3idx(p1, p2)] = acc;
         }
-        wn2[pc] = acc;
-      }
       T w3[2][4];  // [i1][p2]
 #pragma unroll
       for (int i1 = 0; i1 < 2; ++i1)
 #pragma unroll
         for (int p2 = 0; p2 < 4; ++p2) {
           T acc = T(0);
-          for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[ix.pair3_idx[p1][p2]], tb.PF[p1][i1], acc);
+#pragma unroll
+          for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[p3idx(p1, p2)], tb.PF[p1][i1], acc);
           w3[i1][p2] = acc;
         }
       // G part per face time point
       T gv[2][2][2];  // [it][i1][i2]
 #pragma unroll
       for (int tq = 0; tq < 2; ++tq) {
-        T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index pair2_idx[p1][p2]
-#pragma unroll 1
-        for (int pc = 0; pc < 6; ++pc) {
-          int p1 = ix.pair2[pc][0], p2 = ix.pair2[pc][1];
-          T acc = T(0);
-          for (int an = 0; an <= 2 - p1 - p2; ++an) {
-            int abc[3];
-            abc[d] = an;
-            abc[t1] = p1;
-            abc[t2] = p2;
-            acc = fma(gt[(v * 2 + tq) * 10 + ix.tri_idx[abc[0]][abc[1]][abc[2]]], tb.PE[an][side], acc);
+        const T* gtv = gt + (v * 2 + tq) * 10;
+        T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index p2idx(p1, p2)
+#pragma unroll
+        for (int p2 = 0; p2 <= 2; ++p2)
+#pragma unroll
+          for (int p1 = 0; p1 <= 2 - p2; ++p1) {
+            T acc = T(0);
+#pragma unroll
+            for (int an = 0; an <= 2 - p1 - p2; ++an) {
+              const int m = d == 0 ? tri2idx(an, p1, p2) : d == 1 ? tri2idx(p1, an, p2) : tri2idx(p1, p2, an);
+              acc = fma(gtv[m], tb.PE[an][side], acc);
+            }
+            gn2[p2idx(p1, p2)] = acc;
           }
-          gn2[pc] = acc;
-        }
 #pragma unroll
         for (int i1 = 0; i1 < 2; ++i1) {
           T g3[3];
 #pragma unroll
           for (int p2 = 0; p2 < 3; ++p2) {
             T acc = T(0);
-            for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[ix.pair2_idx[p1][p2]], tb.PF[p1][i1], acc);
+#pragma unroll
+            for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[p2idx(p1, p2)], tb.PF[p1][i1], acc);
             g3[p2] = acc;
           }
 #pragma unroll
