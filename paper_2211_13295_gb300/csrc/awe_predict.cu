@@ -332,10 +332,6 @@ struct FactIdx {
   // (offsets into the w / g rows, 255 = none), [4] w of the mode three degrees
   // up (b = 0 only), [5] the derivative factor of the first (1, 2 or 3)
   uint8_t mass_src[3][6][16];
-  // projection (fact_project): first axis of each of the 9 flux row sets; per
-  // (d, v') its row set, whether d is the lower of the two axes P1 leaves, and
-  // whether the P2 axis is above the P1 axis (transverse modes swapped in Y3)
-  int8_t p1c1[9], p2row[12], p2lo[12], p2swap[12];
 };
 __constant__ FactIdx c_fidx;
 
@@ -391,6 +387,75 @@ __host__ __device__ constexpr int tri2_r(int t) {
 __host__ __device__ constexpr int pair2_p(int pe) { return pe < 3 ? pe : pe < 5 ? pe - 3 : 0; }
 __host__ __device__ constexpr int pair2_e(int pe) { return pe < 3 ? 0 : pe < 5 ? 1 : 2; }
 
+// The same enumerations decoded with integer arithmetic on packed constants
+// (2 or 4 bits per entry), for the strided item loops: an index table in
+// shared memory would put a dependent load in front of every operand load.
+__host__ __device__ constexpr unsigned long long pack_bits(int n, int bits, int which) {
+  unsigned long long k = 0;
+  for (int i = 0; i < n; ++i) {
+    int v = 0;
+    switch (which) {
+      case 0: v = tri2_p(i); break;
+      case 1: v = tri2_q(i); break;
+      case 2: v = tri2_r(i); break;
+      default: v = 0;
+    }
+    k |= (unsigned long long)v << (bits * i);
+  }
+  return k;
+}
+// projection axes of the 9 flux row sets and the (d, v') combinations (fact_project)
+__host__ __device__ constexpr int p1c1_of(int r) { return r == 2 || r == 4 || r == 8 ? 1 : r == 5 ? 0 : 2; }
+__host__ __device__ constexpr int p2row_of(int dv) {
+  return dv % 4 == 3 ? 6 + dv / 4
+       : dv % 4 == dv / 4 ? dv / 4
+       : 3 + dv % 4 + dv / 4 - 1;
+}
+__host__ __device__ constexpr bool p2lo_of(int dv) {   // d is the lower of the two axes P1 leaves
+  return dv / 4 == (p1c1_of(p2row_of(dv)) == 0 ? 1 : 0);
+}
+__host__ __device__ constexpr bool p2swap_of(int dv) {  // the P2 axis is above the P1 axis
+  return (p2lo_of(dv) ? (p1c1_of(p2row_of(dv)) == 2 ? 1 : 2) : (p1c1_of(p2row_of(dv)) == 0 ? 1 : 0)) >
+         p1c1_of(p2row_of(dv));
+}
+__host__ __device__ constexpr unsigned long long pack_proj(int which) {
+  unsigned long long k = 0;
+  for (int i = 0; i < 12; ++i) {
+    const unsigned long long v = which == 0 ? (i < 9 ? p1c1_of(i) : 0)
+                               : which == 1 ? p2row_of(i)
+                               : which == 2 ? p2lo_of(i) : p2swap_of(i);
+    k |= v << (4 * i);
+  }
+  return k;
+}
+constexpr unsigned long long kTri2P = pack_bits(10, 2, 0), kTri2Q = pack_bits(10, 2, 1), kTri2R = pack_bits(10, 2, 2);
+constexpr unsigned long long kP1C1 = pack_proj(0), kP2Row = pack_proj(1), kP2Lo = pack_proj(2), kP2Swap = pack_proj(3);
+__host__ __device__ __forceinline__ int unpack(unsigned long long k, int bits, int i) {
+  return (int)((k >> (bits * i)) & ((1ull << bits) - 1));
+}
+// index of (a, b, c), a + b + c <= 2, c outermost (= tri2idx)
+__host__ __device__ __forceinline__ int tri2_fast(int a, int b, int c) {
+  return (c == 0 ? 0 : c == 1 ? 6 : 9) + b * (3 - c) - (b * (b - 1)) / 2 + a;
+}
+// G-mode (a, b, c, e) of degree <= 2 (= gmidx)
+__host__ __device__ __forceinline__ int gm_fast(int a, int b, int c, int e) {
+  return e == 0 ? tri2_fast(a, b, c) : e == 1 ? 10 + (c ? 3 : b ? 2 : a) : 14;
+}
+// exponents of G-mode i (15 modes, e outermost)
+__host__ __device__ constexpr unsigned long long pack_gm(int k) {
+  unsigned long long r = 0;
+  int i = 0;
+  for (int e = 0; e <= 2; ++e)
+    for (int c = 0; c <= 2 - e; ++c)
+      for (int b = 0; b <= 2 - e - c; ++b)
+        for (int a = 0; a <= 2 - e - b - c; ++a) {
+          const int v = k == 0 ? a : k == 1 ? b : k == 2 ? c : e;
+          r |= (unsigned long long)v << (2 * i++);
+        }
+  return r;
+}
+constexpr unsigned long long kGmA = pack_gm(0), kGmB = pack_gm(1), kGmC = pack_gm(2), kGmE = pack_gm(3);
+
 // Mass row of the new G.  The mass flux of direction d is the momentum
 // q_{1+d} = w_{1+d} - sum_g g_{1+d} P_a P_b P_c I_e(tau): a polynomial of total
 // degree <= 3 in (x, y, z, tau), the space the fluxes are projected onto.  The
@@ -403,7 +468,7 @@ __host__ __device__ constexpr int pair2_e(int pe) { return pe < 3 ? 0 : pe < 5 ?
 // different G-modes do not diverge.  Reads the previous G (rows 1..3) and w.
 template <typename T>
 __device__ __forceinline__ T mass_gmode(const T* z, const FactIdx& ix, int b, const T lam[3]) {
-  const int e = ix.gm[b][3];
+  const int e = unpack(kGmE, 2, b);
   const T* zw = z + FactSmem<T>::W;
   const T* zg = z + FactSmem<T>::G;
   T acc = T(0);
@@ -460,7 +525,7 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
     const int a0 = n2 & 3, a1 = n2 >> 2;
 #pragma unroll 1
     for (int r = vh ? 5 : 0; r < (vh ? 9 : 5); ++r) {
-      const int c1 = ix.p1c1[r];
+      const int c1 = unpack(kP1C1, 4, r);
       const int str = 3 << (2 * c1);
       const int base = c1 == 0 ? 4 * a0 + 16 * a1 : c1 == 1 ? a0 + 16 * a1 : a0 + 4 * a1;
       const T* yv = Y1 + (r * 64 + base) * 3;
@@ -482,8 +547,8 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
 #pragma unroll 2
     for (int it = lane; it < 9 * 16 * NPE; it += 32) {
       const int pe = it % NPE, rest = it / NPE, n2 = rest % 16, r = rest / 16;
-      const int p = ix.pair2[pe][0], e = ix.pair2[pe][1];
-      const int c1 = ix.p1c1[r];
+      const int p = pair2_p(pe), e = pair2_e(pe);
+      const int c1 = unpack(kP1C1, 4, r);
       const int a0 = n2 & 3, a1 = n2 >> 2;
       const int str = 3 << (2 * c1);
       const int base = c1 == 0 ? 4 * a0 + 16 * a1 : c1 == 1 ? a0 + 16 * a1 : a0 + 4 * a1;
@@ -500,8 +565,8 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
 #pragma unroll 1
     for (int it = lane; it < 48; it += 32) {
       const int n1 = it & 3, dv = it >> 2;
-      const int r = ix.p2row[dv];
-      const bool lo = ix.p2lo[dv] != 0, swap = ix.p2swap[dv] != 0;
+      const int r = unpack(kP2Row, 4, dv);
+      const bool lo = unpack(kP2Lo, 4, dv) != 0, swap = unpack(kP2Swap, 4, dv) != 0;
       const int nbase = lo ? n1 : 4 * n1, nstr = lo ? 4 : 1;
       const T* y2 = Y2 + r * 16 * 6;
       T y[NPE][4];  // every operand once
@@ -526,15 +591,15 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
     for (int it = lane; it < 12 * 4 * NTR; it += 32) {
       // tr = (p, qq, e): p the mode along c2 (this step), qq along c1 (P1)
       const int tr = it % NTR, rest = it / NTR, n1 = rest % 4, dv = rest / 4;
-      const int p = ix.tri2[tr][0], qq = ix.tri2[tr][1], e = ix.tri2[tr][2];
-      const int r = ix.p2row[dv];
-      const int pe = ix.pair2_idx[qq][e];
-      const bool lo = ix.p2lo[dv] != 0;
+      const int p = unpack(kTri2P, 2, tr), qq = unpack(kTri2Q, 2, tr), e = unpack(kTri2R, 2, tr);
+      const int r = unpack(kP2Row, 4, dv);
+      const int pe = p2idx(qq, e);
+      const bool lo = unpack(kP2Lo, 4, dv) != 0;
       const T* y2 = Y2 + r * 16 * 6 + pe;
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc = fma(y2[(lo ? n1 + 4 * m : m + 4 * n1) * 6], tb.WPN[p][m], acc);
-      Y3[(dv * 4 + n1) * 10 + (ix.p2swap[dv] ? ix.tri_idx[qq][p][e] : tr)] = acc;
+      Y3[(dv * 4 + n1) * 10 + (unpack(kP2Swap, 4, dv) ? tri2_fast(qq, p, e) : tr)] = acc;
     }
   }
   __syncwarp();
@@ -542,10 +607,10 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   for (int it = lane; it < 4 * NGE; it += 32) {
     int b = it % NGE;
     int v = it / NGE;
-    int a = ix.gm[b][0], bb = ix.gm[b][1], c = ix.gm[b][2], e = ix.gm[b][3];
+    const int a = unpack(kGmA, 2, b), bb = unpack(kGmB, 2, b), c = unpack(kGmC, 2, b), e = unpack(kGmE, 2, b);
     int slack = 3 - (a + bb + c + e);
     T s0 = T(0), s1 = T(0), s2 = T(0);
-    int t0 = ix.tri_idx[bb][c][e], t1 = ix.tri_idx[a][c][e], t2 = ix.tri_idx[a][bb][e];
+    const int t0 = tri2_fast(bb, c, e), t1 = tri2_fast(a, c, e), t2 = tri2_fast(a, bb, e);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       s0 = fma(Y3[((0 * 4 + v) * 4 + m) * 10 + t0], tb.QN[a][slack][m], s0);
@@ -777,9 +842,9 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
 #pragma unroll 2
         for (int it = lane; it < 200; it += 32) {
           int t = it % 4, rest = it / 4, tr = rest % 10, v = rest / 10;
-          int a = ix.tri2[tr][0], b = ix.tri2[tr][1], c = ix.tri2[tr][2];
+          const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
           T acc = T(0);
-          for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + ix.gidx[a][b][c][e]], tb.IT[e][t], acc);
+          for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + gm_fast(a, b, c, e)], tb.IT[e][t], acc);
           A[it] = acc;
         }
       }
@@ -807,9 +872,9 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
 #pragma unroll 2
         for (int it = lane; it < 480; it += 32) {
           int t = it % 4, rest = it / 4, pc = rest % 6, rest2 = rest / 6, i = rest2 % 4, v = rest2 / 4;
-          int b = ix.pair2[pc][0], c = ix.pair2[pc][1];
+          const int b = pair2_p(pc), c = pair2_e(pc);
           T acc = T(0);
-          for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + ix.tri_idx[a][b][c]) * 4 + t], tb.PN[a][i], acc);
+          for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + tri2_fast(a, b, c)) * 4 + t], tb.PN[a][i], acc);
           B[it] = acc;
         }
       }
@@ -842,7 +907,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
           int t = it % 4, rest = it / 4, c = rest % 3, rest2 = rest / 3, j = rest2 % 4, rest3 = rest2 / 4;
           int i = rest3 % 4, v = rest3 / 4;
           T acc = T(0);
-          for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + ix.pair2_idx[b][c]) * 4 + t], tb.PN[b][j], acc);
+          for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + p2idx(b, c)) * 4 + t], tb.PN[b][j], acc);
           C[it] = acc;
         }
       }
@@ -934,9 +999,9 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
     T* gt = fv + 240;                     // [v][it][tri] time-integrated G, 100
     for (int it = lane; it < 100; it += 32) {
       int tr = it % 10, rest = it / 10, tq = rest % 2, v = rest / 2;
-      int a = ix.tri2[tr][0], b = ix.tri2[tr][1], c = ix.tri2[tr][2];
+      const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
       T acc = T(0);
-      for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + ix.gidx[a][b][c][e]], tb.ITF[e][tq], acc);
+      for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + gm_fast(a, b, c, e)], tb.ITF[e][tq], acc);
       gt[it] = acc;
     }
     __syncwarp();
@@ -1096,20 +1161,6 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
       }
     }
   }
-  // projection axes (fact_project)
-  const int c1tab[9] = {2, 2, 1, 2, 1, 0, 2, 2, 1};
-  for (int r = 0; r < 9; ++r) h.p1c1[r] = (int8_t)c1tab[r];
-  for (int d = 0; d < 3; ++d)
-    for (int v = 0; v < 4; ++v) {
-      const int lo_ = v < d ? v : d, hi_ = v < d ? d : v;
-      const int r = v == 3 ? 6 + d : v == d ? d : 3 + lo_ + hi_ - 1;
-      const int c1 = c1tab[r];
-      const int alo = c1 == 0 ? 1 : 0, ahi = c1 == 2 ? 1 : 2;   // the two axes other than c1
-      const int c2 = d == alo ? ahi : alo;
-      h.p2row[d * 4 + v] = (int8_t)r;
-      h.p2lo[d * 4 + v] = (int8_t)(d == alo);
-      h.p2swap[d * 4 + v] = (int8_t)(c2 > c1);
-    }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_fidx, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
