@@ -346,8 +346,11 @@ __device__ __forceinline__ bool state_physical5(const T* u, T gm1) {
 // leave some lanes idle in a few stages; that pays in FP32, where the
 // kernel is issue-bound, but not in FP64, where the DP pipe is charged
 // per warp instruction whatever the active lane count.
-enum : unsigned { kStT2 = 1, kStE1 = 2, kStE2 = 4, kStE3 = 8, kStP1 = 16, kStP2 = 32 };
-template <typename T> constexpr unsigned kStatic = sizeof(T) == 4 ? 0x3Fu : 0u;
+enum : unsigned { kStT2 = 1, kStE1 = 2, kStE2 = 4, kStE3 = 8, kStP1 = 16, kStP2 = 32, kStT1 = 64 };
+// FP64 takes the static forms where their idle lanes cost less than the
+// strided forms' lane-dependent trip counts (E1-E3, T1, T2: a masked lane
+// still costs its DP pipe slot); P1 and P2 stay strided (fixed trip counts).
+template <typename T> constexpr unsigned kStatic = sizeof(T) == 4 ? 0x7Fu : (kStT1 | kStT2 | kStE1 | kStE2 | kStE3);
 
 // compile-time positions in the enumerations used by the factorised kernel
 __host__ __device__ constexpr int p3idx(int b, int c) { return c * 4 - c * (c - 1) / 2 + b; }   // b+c <= 3, c outer
@@ -722,13 +725,32 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
     {
       T* T1 = z + FactSmem<T>::R1;        // [v][i][pair3]   200
       T* T2 = T1 + 200;                   // [v][i][j][c]    320
+      if constexpr ((kStatic<T> & kStT1) != 0) {
+        // T1[v][i][(b,c)]: lanes own (i, v), compile-time (b, c, a)
+        if (lane < 20) {
+          const int i = lane & 3, v = lane >> 2;
+          T pni[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) pni[a] = tb.PN[a][i];
+#pragma unroll
+          for (int c = 0; c <= 3; ++c)
+#pragma unroll
+            for (int b = 0; b <= 3 - c; ++b) {
+              T acc = T(0);
+#pragma unroll
+              for (int a = 0; a <= 3 - b - c; ++a) acc = fma(sw[v * 20 + simplex_idx(3, a, b, c)], pni[a], acc);
+              T1[(v * 4 + i) * 10 + p3idx(b, c)] = acc;
+            }
+        }
+      } else {
 #pragma unroll 2
-      for (int it = lane; it < 200; it += 32) {
-        int pc = it % 10, rest = it / 10, i = rest % 4, v = rest / 4;
-        int b = ix.pair3[pc][0], c = ix.pair3[pc][1];
-        T acc = T(0);
-        for (int a = 0; a <= 3 - b - c; ++a) acc = fma(sw[v * 20 + ix.sm3_idx[a][b][c]], tb.PN[a][i], acc);
-        T1[it] = acc;
+        for (int it = lane; it < 200; it += 32) {
+          int pc = it % 10, rest = it / 10, i = rest % 4, v = rest / 4;
+          int b = ix.pair3[pc][0], c = ix.pair3[pc][1];
+          T acc = T(0);
+          for (int a = 0; a <= 3 - b - c; ++a) acc = fma(sw[v * 20 + ix.sm3_idx[a][b][c]], tb.PN[a][i], acc);
+          T1[it] = acc;
+        }
       }
       __syncwarp();
       if constexpr ((kStatic<T> & kStT2) != 0) {
@@ -760,13 +782,24 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
           T pnk[4];
 #pragma unroll
           for (int c = 0; c < 4; ++c) pnk[c] = tb.PN[c][k];
-#pragma unroll 1
-          for (int v = 0; v < 5; ++v) {
-            const T* t2 = T2 + ((v * 4 + i) * 4 + j) * 4;
-            T acc = T(0);
+          if constexpr (FactSmem<T>::WN_REG) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc = fma(t2[c], pnk[c], acc);
-            swn[v * 64 + s] = acc;
+            for (int v = 0; v < 5; ++v) {
+              const T* t2 = T2 + ((v * 4 + i) * 4 + j) * 4;
+              T acc = T(0);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc = fma(t2[c], pnk[c], acc);
+              wnr[hs][v] = acc;
+            }
+          } else {
+#pragma unroll 1
+            for (int v = 0; v < 5; ++v) {
+              const T* t2 = T2 + ((v * 4 + i) * 4 + j) * 4;
+              T acc = T(0);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc = fma(t2[c], pnk[c], acc);
+              swn[v * 64 + s] = acc;
+            }
           }
         }
       } else {
