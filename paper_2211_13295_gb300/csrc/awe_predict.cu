@@ -469,30 +469,41 @@ constexpr unsigned long long kGmA = pack_gm(0), kGmB = pack_gm(1), kGmC = pack_g
 // Same value as projecting the node fluxes, up to rounding, without the node
 // work.  Branch-free over a source table (FactIdx::mass_src), so lanes with
 // different G-modes do not diverge.  Reads the previous G (rows 1..3) and w.
+// One direction's term, lamd * d/dx_d of the momentum q_{1+d}, of G-mode b
+// (0 for the unused column b = 15).  The coefficient of L_e of a source mode
+// is cw w + c0 g_0 + c1 g_1 + c2 g_2 with (1, -1/2, 1/6, 0), (0, -1/2, 0, 1/10),
+// (0, 0, -1/6, 0) for e = 0, 1, 2.
 template <typename T>
-__device__ __forceinline__ T mass_gmode(const T* z, const FactIdx& ix, int b, const T lam[3]) {
+__device__ __forceinline__ T mass_gmode_dir(const T* z, const FactIdx& ix, int b, int d, T lamd) {
   const int e = unpack(kGmE, 2, b);
   const T* zw = z + FactSmem<T>::W;
   const T* zg = z + FactSmem<T>::G;
-  T acc = T(0);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int ow = ix.mass_src[d][0][b], o0 = ix.mass_src[d][1][b], o1 = ix.mass_src[d][2][b];
-    const int o2 = ix.mass_src[d][3][b], o3 = ix.mass_src[d][4][b];
-    const T w = ow != 255 ? zw[ow] : T(0);
-    const T g0 = o0 != 255 ? zg[o0] : T(0);
-    const T g1 = o1 != 255 ? zg[o1] : T(0);
-    const T g2 = o2 != 255 ? zg[o2] : T(0);
-    const T w3 = o3 != 255 ? zw[o3] : T(0);
-    // coefficient of L_e of the source mode
-    const T m0 = fma(T(1.0 / 6.0), g1, fma(T(-0.5), g0, w));
-    const T m1 = fma(T(0.1), g2, T(-0.5) * g0);
-    const T m2 = T(-1.0 / 6.0) * g1;
-    const T m = e == 0 ? m0 : e == 1 ? m1 : m2;
-    const T sd = fma(T(ix.mass_src[d][5][b]), m, T(0.1) * w3);
-    acc = fma(lam[d], sd, acc);
-  }
-  return acc;
+  const int ow = ix.mass_src[d][0][b], o0 = ix.mass_src[d][1][b], o1 = ix.mass_src[d][2][b];
+  const int o2 = ix.mass_src[d][3][b], o3 = ix.mass_src[d][4][b];
+  const T w = ow != 255 ? zw[ow] : T(0);
+  const T g0 = o0 != 255 ? zg[o0] : T(0);
+  const T g1 = o1 != 255 ? zg[o1] : T(0);
+  const T g2 = o2 != 255 ? zg[o2] : T(0);
+  const T w3 = o3 != 255 ? zw[o3] : T(0);
+  const T cw = e == 0 ? T(1) : T(0);
+  const T c0 = e == 2 ? T(0) : T(-0.5);
+  const T c1 = e == 0 ? T(1.0 / 6.0) : e == 2 ? T(-1.0 / 6.0) : T(0);
+  const T c2 = e == 1 ? T(0.1) : T(0);
+  const T m = fma(c2, g2, fma(c1, g1, fma(c0, g0, cw * w)));
+  return lamd * fma(T(ix.mass_src[d][5][b]), m, T(0.1) * w3);
+}
+// Mass row of G-mode (lane & 15): lanes 0-15 take directions 0 and 1, lanes
+// 16-31 direction 2, combined by one shuffle (valid in lanes < 15).  Every
+// lane runs the same instructions: a masked lane would cost its DP slot.
+template <typename T>
+__device__ __forceinline__ T mass_gmode(const T* z, const FactIdx& ix, int lane, const T lam[3]) {
+  const int b = lane & 15;
+  const bool lo = lane < 16;
+  const T p0 = mass_gmode_dir<T>(z, ix, b, lo ? 0 : 2, lo ? lam[0] : lam[2]);
+  const T p1 = mass_gmode_dir<T>(z, ix, b, lo ? 1 : 2, lo ? lam[1] : lam[2]);
+  T part = lo ? p0 + p1 : p0;
+  part += __shfl_down_sync(0xffffffffu, part, 16);
+  return part;
 }
 
 // Picard projection of the node fluxes of the momentum and energy rows (the
@@ -516,7 +527,7 @@ __device__ __forceinline__ void fact_project(T* z, const Tabs<T>& tb, const Fact
   T* Y2 = z + FactSmem<T>::R1;               // [r][n2][pe]         (pe stride 6)
   T* Y3 = z + FactSmem<T>::R2;               // [d][v'][n1][tri]    (tri stride 10; Y1 is dead)
   // the mass row from the previous G, before P3 overwrites it
-  const T gmass = lane < NGE ? mass_gmode<T>(z, ix, lane, lam) : T(0);
+  const T gmass = mass_gmode<T>(z, ix, lane, lam);   // all lanes take part (shuffle)
   // Static lane mappings (kStatic): P1 lanes own (n2, a group of row sets),
   // P2 lanes own (n1, d, v'); the remaining indices are compile-time loops, so
   // the basis values are uniform constant-bank operands.
