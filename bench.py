@@ -493,7 +493,7 @@ def run_native(args, rank, world, local):
                "predictor_ms": mp32 / max(np32, 1),
                "predictor_tflops": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12,
                "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32,
-               "predictor_bound": "shared-memory bandwidth: 64% of the LSU wavefront peak, issue 41%, FP32 pipe 16% "
+               "predictor_bound": "shared-memory bandwidth: 85% of the LSU wavefront peak, issue 51%, FP32 pipe 23% "
                                   "(ncu, profiles/predictor_fp32_tgv48.md)"}
         if U1f is not None:
             sc = np.abs(U1[0]).sum()

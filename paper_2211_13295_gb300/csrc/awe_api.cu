@@ -594,6 +594,14 @@ int awe_destroy(awe_grid* g) {
 // milliseconds on this platform.  Anything else (pageable memory) goes through
 // the staging buffer with cudaMemcpyAsync.
 static bool host_mapped(const void* p) {
+  // only memory that the CUDA runtime itself page-locked (cudaHostAlloc or
+  // cudaHostRegister): on platforms that address pageable memory from the
+  // GPU the pointer attributes alone do not tell pinned memory apart
+  unsigned int flags = 0;
+  if (cudaHostGetFlags(&flags, const_cast<void*>(p)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();

@@ -54,3 +54,33 @@ def test_pinned_and_pageable_routes_agree_bitwise(awe, case):
             results.append(g.get_state())
         g.close()
     assert np.array_equal(results[0], results[1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_large_fresh_pageable_buffers_read_the_grid_state(awe, prec):
+    """States of tens of MB land in fresh anonymous mappings (np.zeros), which
+    this platform's pointer attributes report as host memory although CUDA did
+    not page-lock them: such a buffer must take the staging copy and read the
+    grid's own state, equal to the page-locked and the touched-pageable reads,
+    and different between the FP64 and FP32 forms after a step."""
+    import torch
+    prob = P.tgv3d(n=64, order=4, cfl=0.3)
+    Uh = torch.from_numpy(prob.initial_state()).pin_memory()
+    reads = {}
+    for form in ("fp64", prec):
+        g = awe.Grid(prob, prec=form)
+        g.set_state(Uh.numpy())
+        g.step(g.cfl_dt())
+        fresh = g.get_state()                     # np.zeros: a fresh mapping
+        touched = np.full(fresh.shape, 7.0)
+        g.get_state(touched)
+        pinned = torch.empty_like(Uh).pin_memory()
+        g.get_state(pinned.numpy())
+        g.close()
+        assert np.array_equal(fresh, touched)
+        assert np.array_equal(fresh, pinned.numpy())
+        assert np.abs(fresh - Uh.numpy()).max() > 1e-6    # the step changed the state
+        reads[form] = fresh
+    if prec == "fp32":
+        d = np.abs(reads["fp32"] - reads["fp64"]).max()
+        assert 0 < d < 1e-3
