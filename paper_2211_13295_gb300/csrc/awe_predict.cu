@@ -322,11 +322,11 @@ template <typename T> struct FactSmem {
   static constexpr int SIZE = R2 + 1728;               // 2863 (FP64), 3184 (FP32)
 };
 
-// index tables copied to shared memory once per block (lane-divergent reads
-// of constant memory are serialised; shared memory is not)
+// the mass-row source table, copied to shared memory once per block
+// (lane-divergent reads of constant memory are serialised; shared memory is
+// not).  The other enumerations are compile-time functions or packed
+// constants (p3idx, tri2idx, gmidx, kTri2P, ...).
 struct FactIdx {
-  int8_t sm3[20][3], pair3[10][2], tri2[10][3], pair2[6][2], gm[15][4];
-  int8_t gidx[3][3][3][3], tri_idx[3][3][3], pair2_idx[3][3], pair3_idx[4][4], sm3_idx[4][4][4];
   // sources of the mass row of G (mass_gmode), per direction d and G-mode b:
   // [0] w, [1..3] g with e = 0..2 of the momentum mode one degree up in d
   // (offsets into the w / g rows, 255 = none), [4] w of the mode three degrees
@@ -340,17 +340,16 @@ __device__ __forceinline__ bool state_physical5(const T* u, T gm1) {
   return state_physical<3, T>(u, gm1);
 }
 
-// Stages of the factorised kernel with static lane mappings (each lane owns
-// fixed indices, the rest are compile-time loops with constant-bank basis
-// operands) versus strided item loops over all 32 lanes.  The static forms
-// leave some lanes idle in a few stages; that pays in FP32, where the
-// kernel is issue-bound, but not in FP64, where the DP pipe is charged
-// per warp instruction whatever the active lane count.
-enum : unsigned { kStT2 = 1, kStE1 = 2, kStE2 = 4, kStE3 = 8, kStP1 = 16, kStP2 = 32, kStT1 = 64 };
-// FP64 takes the static forms where their idle lanes cost less than the
-// strided forms' lane-dependent trip counts (E1-E3, T1, T2: a masked lane
-// still costs its DP pipe slot); P1 and P2 stay strided (fixed trip counts).
-template <typename T> constexpr unsigned kStatic = sizeof(T) == 4 ? 0x7Fu : (kStT1 | kStT2 | kStE1 | kStE2 | kStE3);
+// Lane mappings of the factorised kernel.  The contraction stages of w at the
+// nodes (T1, T2) and of the G evaluation (E1-E3) use static mappings: each
+// lane owns fixed indices and the rest are compile-time loops with
+// constant-bank basis operands; some lanes idle, but every lane runs the same
+// trip counts.  The two projection steps choose per precision: static in FP32
+// (issue-bound: fewer loads and address computations), strided item loops over
+// all 32 lanes in FP64 (fixed four-term sums, so no lane waits; the DP pipe is
+// charged per warp instruction whatever the active lane count).
+enum : unsigned { kStP1 = 1, kStP2 = 2 };
+template <typename T> constexpr unsigned kStatic = sizeof(T) == 4 ? (kStP1 | kStP2) : 0u;
 
 // compile-time positions in the enumerations used by the factorised kernel
 __host__ __device__ constexpr int p3idx(int b, int c) { return c * 4 - c * (c - 1) / 2 + b; }   // b+c <= 3, c outer
@@ -736,7 +735,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
     {
       T* T1 = z + FactSmem<T>::R1;        // [v][i][pair3]   200
       T* T2 = T1 + 200;                   // [v][i][j][c]    320
-      if constexpr ((kStatic<T> & kStT1) != 0) {
+      {
         // T1[v][i][(b,c)]: lanes own (i, v), compile-time (b, c, a)
         if (lane < 20) {
           const int i = lane & 3, v = lane >> 2;
@@ -753,18 +752,9 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
               T1[(v * 4 + i) * 10 + p3idx(b, c)] = acc;
             }
         }
-      } else {
-#pragma unroll 2
-        for (int it = lane; it < 200; it += 32) {
-          int pc = it % 10, rest = it / 10, i = rest % 4, v = rest / 4;
-          int b = ix.pair3[pc][0], c = ix.pair3[pc][1];
-          T acc = T(0);
-          for (int a = 0; a <= 3 - b - c; ++a) acc = fma(sw[v * 20 + ix.sm3_idx[a][b][c]], tb.PN[a][i], acc);
-          T1[it] = acc;
-        }
       }
       __syncwarp();
-      if constexpr ((kStatic<T> & kStT2) != 0) {
+      {
         {
           // T2[v][i][j][c]: lanes own (i, j) and half of the variables
           const int i = lane & 3, j = (lane >> 2) & 3, h = lane >> 4;
@@ -813,28 +803,6 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
             }
           }
         }
-      } else {
-#pragma unroll 2
-        for (int it = lane; it < 320; it += 32) {
-          int c = it % 4, rest = it / 4, j = rest % 4, rest2 = rest / 4, i = rest2 % 4, v = rest2 / 4;
-          T acc = T(0);
-          for (int b = 0; b <= 3 - c; ++b) acc = fma(T1[(v * 4 + i) * 10 + ix.pair3_idx[b][c]], tb.PN[b][j], acc);
-          T2[it] = acc;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int hs = 0; hs < 2; ++hs) {
-          const int s = lane + 32 * hs;
-          const int i = s & 3, j = (s >> 2) & 3, k = s >> 4;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            T acc = T(0);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc = fma(T2[((v * 4 + i) * 4 + j) * 4 + c], tb.PN[c][k], acc);
-            if constexpr (FactSmem<T>::WN_REG) wnr[hs][v] = acc;
-            else swn[v * 64 + s] = acc;
-          }
-        }
       }
       __syncwarp();
     }
@@ -867,7 +835,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
       T* B = A + 200;               // [v][i][pair2][t]   480 (dead before Y1 is written)
       T* C = z + FactSmem<T>::R1;   // [v][i][j][c][t]    960
       // E1: A[v][(a,b,c)][t] = sum_e g[(a,b,c,e)] I_e(tau_t); lanes own (t, v)
-      if constexpr ((kStatic<T> & kStE1) != 0) {
+      {
         if (lane < 20) {
           const int t = lane & 3, v = lane >> 2;
           T it_[3];
@@ -882,19 +850,10 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
             A[(v * 10 + tr) * 4 + t] = acc;
           }
         }
-      } else {
-#pragma unroll 2
-        for (int it = lane; it < 200; it += 32) {
-          int t = it % 4, rest = it / 4, tr = rest % 10, v = rest / 10;
-          const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
-          T acc = T(0);
-          for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + gm_fast(a, b, c, e)], tb.IT[e][t], acc);
-          A[it] = acc;
-        }
       }
       __syncwarp();
       // E2: B[v][i][(b,c)][t] = sum_a A[(a,b,c)][t] P_a(x_i); lanes own (i, t, half of v)
-      if constexpr ((kStatic<T> & kStE2) != 0) {
+      {
         {
           const int i = lane & 3, t = (lane >> 2) & 3, h = lane >> 4;
           T pni[3];
@@ -912,19 +871,10 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
             }
           }
         }
-      } else {
-#pragma unroll 2
-        for (int it = lane; it < 480; it += 32) {
-          int t = it % 4, rest = it / 4, pc = rest % 6, rest2 = rest / 6, i = rest2 % 4, v = rest2 / 4;
-          const int b = pair2_p(pc), c = pair2_e(pc);
-          T acc = T(0);
-          for (int a = 0; a <= 2 - b - c; ++a) acc = fma(A[(v * 10 + tri2_fast(a, b, c)) * 4 + t], tb.PN[a][i], acc);
-          B[it] = acc;
-        }
       }
       __syncwarp();
       // E3: C[v][i][j][c][t] = sum_b B[i][(b,c)][t] P_b(y_j); lanes own (i, j, parity of t)
-      if constexpr ((kStatic<T> & kStE3) != 0) {
+      {
         {
           const int i = lane & 3, j = (lane >> 2) & 3, h = lane >> 4;
           T pnj[3];
@@ -944,15 +894,6 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
               }
             }
           }
-        }
-      } else {
-#pragma unroll 2
-        for (int it = lane; it < 960; it += 32) {
-          int t = it % 4, rest = it / 4, c = rest % 3, rest2 = rest / 3, j = rest2 % 4, rest3 = rest2 / 4;
-          int i = rest3 % 4, v = rest3 / 4;
-          T acc = T(0);
-          for (int b = 0; b <= 2 - c; ++b) acc = fma(B[((v * 4 + i) * 6 + p2idx(b, c)) * 4 + t], tb.PN[b][j], acc);
-          C[it] = acc;
         }
       }
       __syncwarp();
@@ -1147,38 +1088,7 @@ static bool g_fact_tables_ready = false;
 
 static cudaError_t upload_fact_indices(cudaStream_t s) {
   FactIdx h;
-  memset(&h, -1, sizeof(h));
-  int m = 0;
-  for (int c = 0; c <= 3; ++c)
-    for (int b = 0; b <= 3 - c; ++b)
-      for (int a = 0; a <= 3 - b - c; ++a) {
-        h.sm3[m][0] = a; h.sm3[m][1] = b; h.sm3[m][2] = c;
-        h.sm3_idx[a][b][c] = m++;
-      }
-  m = 0;
-  for (int c = 0; c <= 3; ++c)
-    for (int b = 0; b <= 3 - c; ++b) {
-      h.pair3[m][0] = b; h.pair3[m][1] = c;
-      h.pair3_idx[b][c] = m++;
-    }
-  m = 0;
-  for (int r = 0; r <= 2; ++r)
-    for (int qq = 0; qq <= 2 - r; ++qq)
-      for (int p = 0; p <= 2 - r - qq; ++p) {
-        h.tri2[m][0] = p; h.tri2[m][1] = qq; h.tri2[m][2] = r;
-        h.tri_idx[p][qq][r] = m++;
-      }
-  m = 0;
-  for (int e = 0; e <= 2; ++e)
-    for (int p = 0; p <= 2 - e; ++p) {
-      h.pair2[m][0] = p; h.pair2[m][1] = e;
-      h.pair2_idx[p][e] = m++;
-    }
   auto g = st_modes(3, 2);
-  for (int b = 0; b < 15; ++b) {
-    for (int t = 0; t < 4; ++t) h.gm[b][t] = (int8_t)g[b][t];
-    h.gidx[g[b][0]][g[b][1]][g[b][2]][g[b][3]] = b;
-  }
   // mass-row sources (mass_gmode): the momentum mode one degree up in d, and
   // for b = 0 the mode three degrees up (dP3 = 3 P2 + P0/10)
   memset(h.mass_src, 255, sizeof(h.mass_src));
@@ -1195,13 +1105,13 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
         const int deg = abc[0] + abc[1] + abc[2];
         if (deg + e > 3) continue;
         if (k == 1) {
-          h.mass_src[d][4][b] = (uint8_t)((1 + d) * 20 + h.sm3_idx[abc[0]][abc[1]][abc[2]]);
+          h.mass_src[d][4][b] = (uint8_t)((1 + d) * 20 + simplex_idx(3, abc[0], abc[1], abc[2]));
           continue;
         }
         h.mass_src[d][5][b] = (uint8_t)(ad + 1);
-        h.mass_src[d][0][b] = (uint8_t)((1 + d) * 20 + h.sm3_idx[abc[0]][abc[1]][abc[2]]);
+        h.mass_src[d][0][b] = (uint8_t)((1 + d) * 20 + simplex_idx(3, abc[0], abc[1], abc[2]));
         for (int ee = 0; ee < 3; ++ee)
-          if (deg + ee <= 2) h.mass_src[d][1 + ee][b] = (uint8_t)((1 + d) * 15 + h.gidx[abc[0]][abc[1]][abc[2]][ee]);
+          if (deg + ee <= 2) h.mass_src[d][1 + ee][b] = (uint8_t)((1 + d) * 15 + gmidx(abc[0], abc[1], abc[2], ee));
       }
     }
   }
