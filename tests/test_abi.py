@@ -60,3 +60,54 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(awe, "_lib", None)
     with pytest.raises(RuntimeError):
         awe.lib()
+
+
+BAD_CONFIGS = {
+    "dim": lambda c: setattr(c, "dim", 1),
+    "order_high": lambda c: setattr(c, "order", 5),
+    "order_low": lambda c: setattr(c, "order", 1),
+    "gate_at_order_2": lambda c: (setattr(c, "order", 2), setattr(c, "gate", 1)),
+    "prec": lambda c: setattr(c, "prec", 7),
+    "too_few_zones": lambda c: c.n.__setitem__(1, 2),
+    "empty_domain": lambda c: c.hi.__setitem__(0, c.lo[0]),
+    "boundary": lambda c: c.bc.__setitem__(3, 99),
+    "gamma": lambda c: setattr(c, "gamma", 1.0),
+    "picard": lambda c: setattr(c, "picard", 9),
+    "slab": lambda c: setattr(c, "slab", -1),
+    "riemann": lambda c: setattr(c, "riemann", 9),
+    "scheme": lambda c: setattr(c, "scheme", 5),
+    "rk_stages": lambda c: (setattr(c, "scheme", 1), setattr(c, "rk_stages", 4)),
+    "grid_too_large": lambda c: [c.n.__setitem__(d, 1 << 11) for d in range(3)],
+}
+
+
+@pytest.mark.parametrize("case", sorted(BAD_CONFIGS))
+def test_create_rejects_a_bad_config_before_touching_the_device(libawe, case):
+    """awe_create validates the whole configuration before any CUDA call, so
+    every rejection (AWE_ERR_ARG with a message, no handle) runs on a machine
+    without a GPU."""
+    from paper_2211_13295_gb300 import awe
+    from paper_2211_13295_gb300 import problems as P
+    c = awe.make_config(P.tgv3d(n=8, order=4))
+    BAD_CONFIGS[case](c)
+    h = ctypes.c_void_p(1234)
+    libawe.awe_last_error.restype = ctypes.c_char_p
+    rc = libawe.awe_create(ctypes.byref(c), None, ctypes.byref(h))
+    assert rc == -1
+    assert h.value is None
+    assert libawe.awe_last_error(None)
+
+
+def test_create_reports_a_forced_allocation_failure(libawe, monkeypatch):
+    """AWE_FAIL_ALLOC=1 makes awe_create fail as if the device allocation had
+    (AWE_ERR_OOM, no handle), after the configuration checks, before any CUDA
+    call: the out-of-memory path of a caller can be exercised without a GPU."""
+    from paper_2211_13295_gb300 import awe
+    from paper_2211_13295_gb300 import problems as P
+    monkeypatch.setenv("AWE_FAIL_ALLOC", "1")
+    c = awe.make_config(P.tgv3d(n=8, order=4))
+    h = ctypes.c_void_p(1234)
+    libawe.awe_last_error.restype = ctypes.c_char_p
+    assert libawe.awe_create(ctypes.byref(c), None, ctypes.byref(h)) == -3
+    assert h.value is None
+    assert b"AWE_FAIL_ALLOC" in libawe.awe_last_error(None)
