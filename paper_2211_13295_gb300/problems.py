@@ -356,6 +356,38 @@ def _kh_ic(prob, nsub=8):
 
 
 # ---------------------------------------------------------------------------
+# 3D density wave advected along the diagonal (smooth; exact solution known)
+# ---------------------------------------------------------------------------
+def wave3d(n=32, order=4, cfl=0.3, t_end=0.1, amp=0.2, vel=(1.0, 1.0, 1.0)) -> Problem:
+    """rho = 1 + amp sin(2 pi (x + y + z)), constant velocity and pressure p = 1 on
+    the periodic unit cube: an isolated contact whose exact solution at time t
+    is the initial state moved by vel * t.  Every mixed derivative of the
+    density is non-zero, so all cross modes of the reconstruction take part."""
+    return Problem("wave3d", 3, (n, n, n), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), order, cfl=cfl,
+                   t_end=t_end, params={"amp": amp, "vel": tuple(vel)})
+
+
+def wave3d_exact(prob, t):
+    """Zone averages of the exact state at time t (products of sinc factors)."""
+    amp, vel = prob.params["amp"], prob.params["vel"]
+    w = 2.0 * math.pi
+    xs = [_centers(prob, d) - vel[d] * t for d in range(3)]
+    hs = [prob.dx(d) for d in range(3)]
+    damp = 1.0
+    for d in range(3):
+        damp *= np.sinc(w * hs[d] / (2.0 * math.pi))
+    arg = (w * xs[0])[None, None, :] + (w * xs[1])[:, None][None] + (w * xs[2])[:, None, None]
+    rho = 1.0 + amp * damp * np.sin(arg)
+    out = np.zeros(prob.shape())
+    out[0] = rho
+    for d in range(3):
+        out[1 + d] = rho * vel[d]
+    kin = 0.5 * sum(v * v for v in vel)
+    out[4] = 1.0 / (prob.gamma - 1.0) + kin * rho
+    return out
+
+
+# ---------------------------------------------------------------------------
 # free stream
 # ---------------------------------------------------------------------------
 def uniform(dim=2, n=16, order=3, rho=1.0, vel=(0.3, -0.2, 0.1), p=1.0, bc="periodic") -> Problem:
@@ -380,9 +412,10 @@ _IC = {
     "blast3d": _blast_ic,
     "kh3d": _kh_ic,
     "uniform": _uniform_ic,
+    "wave3d": lambda p: wave3d_exact(p, 0.0),
 }
 
 
 def by_name(name: str, **kw) -> Problem:
     return {"vortex2d": vortex2d, "sod": sod, "tgv3d": tgv3d, "dmr": dmr, "blast3d": blast3d,
-            "kh3d": kh3d, "uniform": uniform}[name](**kw)
+            "kh3d": kh3d, "uniform": uniform, "wave3d": wave3d}[name](**kw)
