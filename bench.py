@@ -145,7 +145,8 @@ def workload(n, order=4):
 
 
 def workload_name(prob):
-    return f"tgv3d {prob.n[0]}^3 order {prob.order} HLLC CFL {prob.cfl} periodic"
+    ext = f"{prob.n[0]}^3" if prob.n[2] == prob.n[0] else f"{prob.n[0]}x{prob.n[1]}x{prob.n[2]}"
+    return f"tgv3d {ext} order {prob.order} HLLC CFL {prob.cfl} periodic"
 
 
 def gpu_state(prob):
@@ -335,8 +336,9 @@ def other_configs(world, gate_params):
             g.check()
         except awe.AweError as e:
             status = f"status {e.code}: {e}"
-        d = {"value": world * prob.zones / (ms * 1e-3), "unit": "zone-updates/s", "ms_per_step": ms,
-             "zones": prob.zones, "status": status,
+        # a run that ended in a non-physical state has no rate, only its status
+        d = {"value": world * prob.zones / (ms * 1e-3) if status == "ok" else None, "unit": "zone-updates/s",
+             "ms_per_step": ms if status == "ok" else None, "zones": prob.zones, "status": status,
              "stage_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}}
         if gate:
             fl, tot = g.gate_stats()
@@ -430,14 +432,61 @@ def gated_forms(args, prob, Uh, U1, zones, world):
     return out
 
 
+def slab_decomposition_1gpu(prob, Uh, U1, parts=2, steps=3, warmup=2):
+    """The headline grid split into z-slabs on one GPU (slabs.SlabGrid): the
+    same step through the halo pack/unpack kernels and the dt minimum over
+    the slabs; zone-updates/s, the exchange time, and whether its first step
+    equals the undivided grid's bit for bit."""
+    import torch
+    from paper_2211_13295_gb300 import slabs
+    sg = slabs.SlabGrid(prob, parts)
+    sg.set_state(Uh.numpy())
+    same = None
+    if U1 is not None:
+        dt0 = sg.cfl_dt()
+        sg.step(dt0, sync=True)
+        same = bool(np.array_equal(sg.get_state(), U1))
+        sg.set_state(Uh.numpy())
+        sg.set_time(0.0)
+    sg.cfl_dt()
+    for _ in range(warmup):
+        sg.step(0.0, sync=False)
+    torch.cuda.synchronize()
+    sg.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        sg.step(0.0, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = sg.profile_read()
+    sg.check()
+    sg.close()
+    return {"slabs": parts, "value": prob.zones / (ms * 1e-3), "unit": "zone-updates/s", "ms_per_step": ms,
+            "exchange_ms_per_step": prof["halo_exchange"][1] / steps,
+            "first_step_bitwise_equal_to_undivided": same}
+
+
 def run_native(args, rank, world, local):
     import torch
     from paper_2211_13295_gb300 import awe, build, opcount
+    from paper_2211_13295_gb300 import problems as P
     build.build()
     torch.cuda.set_device(local)
-    prob = workload(args.n, args.order)
-    Uh = gpu_state(prob)
-    grid = awe.Grid(prob, prec=args.form, gate=args.gate)
+    if world > 1:
+        # one grid of n x n x (n * world) zones split into z-slabs, one n^3
+        # slab per GPU: per step one halo exchange (NCCL point-to-point) and
+        # one all-reduce MIN of dt (weak scaling: fixed work per GPU)
+        from paper_2211_13295_gb300 import slabs
+        gprob = P.tgv3d(n=args.n, order=args.order, cfl=0.3, nz=args.n * world)
+        grid = slabs.DistSlabGrid(gprob, rank, world, prec=args.form, gate=False)
+        prob = grid.sub_prob
+        Uh = gpu_state(prob)
+    else:
+        gprob = prob = workload(args.n, args.order)
+        Uh = gpu_state(prob)
+        grid = awe.Grid(prob, prec=args.form, gate=args.gate)
     if args.gate:
         from paper_2211_13295_gb300.gate_train import he_init
         grid.gate_set_weights(he_init(awe.gate_dims(prob.dim, prob.order)[0], 2211))
@@ -445,7 +494,8 @@ def run_native(args, rank, world, local):
     # one explicit step from the initial state for the stated error
     dt0 = grid.cfl_dt()
     grid.step(dt0)
-    U1 = grid.get_state() if rank == 0 and not args.no_cpu else None
+    grid.check()
+    U1 = grid.get_state() if rank == 0 and world == 1 and not args.no_cpu else None
     grid.set_state(Uh.numpy())
     grid.set_time(0.0)
 
@@ -461,13 +511,25 @@ def run_native(args, rank, world, local):
     avg_pred = ms_pred / max(n_pred, 1)
     flops_pred = opcount.predictor_flops_per_launch(prob)
     achieved = flops_pred / (avg_pred * 1e-3) / 1e12
-    traffic = None
+    # DRAM bytes of one predictor launch: not measurable inside this run (ncu
+    # replays kernels); taken from one ncu capture of the same kernel on a
+    # 48^3 grid, scaled to this launch by the box zones it processes, and
+    # labelled as such in the line
+    traffic, traffic_source = None, None
     tr_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_file) and prob.order == 4 and args.form == "fp64":
-        traffic = json.load(open(tr_file)).get("predictor_fp64_per_launch")
+    if os.path.exists(tr_file) and prob.order == 4:
+        tr = json.load(open(tr_file))
+        key = "predictor_fp64_per_launch" if args.form == "fp64" else "predictor_fp32_per_launch"
+        if tr.get(key) is not None and tr.get(key + "_kernel_sha") == opcount.predictor_source_sha():
+            traffic = tr[key]
+            traffic_source = tr.get(key + "_source")
     launches_per_step = sum(v[0] for v in prof.values()) / max(args.steps, 1)
     # kernel launches of the timed region: profiled spans + 1 finalize per step
-    gpu_launches = int(round(sum(v[0] for k, v in prof.items()) + args.steps))
+    gpu_launches = int(round(sum(v[0] for k, v in prof.items() if k != "halo_exchange") + args.steps))
+    if world > 1:
+        # per exchange two pack and two unpack kernels (their ghost fills are
+        # profiled spans already)
+        gpu_launches += 4 * prof["halo_exchange"][0]
 
     grid.set_state(Uh.numpy())
     grid.cfl_dt()
@@ -477,7 +539,8 @@ def run_native(args, rank, world, local):
     grid.close()
 
     forms = {}
-    if not args.no_forms and args.form == "fp64":
+    run_forms = not args.no_forms and args.form == "fp64" and world == 1
+    if run_forms:
         g32 = awe.Grid(prob, prec="fp32")
         g32.set_state(Uh.numpy())
         dtf = g32.cfl_dt()
@@ -492,9 +555,7 @@ def run_native(args, rank, world, local):
                "dtype": "f32 bulk, f64 update/weights/CFL",
                "predictor_ms": mp32 / max(np32, 1),
                "predictor_tflops": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12,
-               "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32,
-               "predictor_bound": "shared-memory bandwidth: 85% of the LSU wavefront peak, issue 51%, FP32 pipe 23% "
-                                  "(ncu, profiles/predictor_fp32_tgv48.md)"}
+               "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32}
         if U1f is not None:
             sc = np.abs(U1[0]).sum()
             f32["rel_l1_vs_fp64_gpu_one_step"] = max(
@@ -504,12 +565,13 @@ def run_native(args, rank, world, local):
                 float(np.abs(U1f[v] - U1[v]).max() / max(np.abs(U1[v]).max(), sci)) for v in range(5))
         forms["fp32_bulk"] = f32
 
-    if not args.no_forms and args.form == "fp64":
+    if run_forms:
         forms.update(gated_forms(args, prob, Uh, U1, zones, world))
         gate_params = forms.pop("_params")
 
-    table2 = table4 = solvers = small = others = None
-    if not args.no_forms and args.form == "fp64":
+    table2 = table4 = solvers = small = others = slab1 = None
+    if run_forms:
+        slab1 = slab_decomposition_1gpu(prob, Uh, U1)
         small = small_grid_graph()
         others = other_configs(world, gate_params)
         table2 = orders_192(args, world)
@@ -547,12 +609,14 @@ def run_native(args, rank, world, local):
             "vs_baseline": None,
             "dtype": "f64" if args.form == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(prob), "n": prob.n[0], "order": prob.order,
-                       "form": args.form, "riemann": "hllc", "parallelism": f"replicas{world}",
+            "config": {"workload": workload_name(gprob), "n": prob.n[0], "order": prob.order,
+                       "form": args.form, "riemann": "hllc",
+                       "parallelism": "one grid" if world == 1 else
+                       f"z-slabs x{world}: one {args.n}^3 slab per GPU, halo exchange + dt MIN per step",
                        "l2": "inputs larger than L2 (state 671 MB, modes 13.7 GB per step)",
                        "l1_vs_oracle_one_step": parity},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
                          "kernel": f"predictor ({'k_predict_fact' if prob.order == 4 else 'k_predict_direct'}"
                                    f"<{'double' if args.form == 'fp64' else 'float'}>)",
                          "peak_source": f"derived: 152 SMs x {'2 FP64' if args.form == 'fp64' else '128 FP32'} FMA/clk x 2 x 2.07 GHz",
@@ -569,9 +633,49 @@ def run_native(args, rank, world, local):
             "ssprk_orders_tgv192_fp64": table4,
             "riemann_tgv192_o4_fp64": solvers,
             "small_grid_cuda_graph": small,
+            "slab_decomposition_1gpu": slab1,
             "other_workloads": others,
         }
+        if world > 1:
+            line["halo_exchange_ms_per_step"] = prof.get("halo_exchange", (0, 0.0))[1] / args.steps
+            line["comm_nranks"] = world
+        # last key: a compact digest of every form and workload, so that the
+        # end of the line (what a log tail keeps) carries all the numbers
+        line["summary"] = summary(line)
         print(json.dumps(line))
+
+
+def _sig(x, k=3):
+    if x is None:
+        return None
+    if isinstance(x, (int, float)) and x != 0 and math.isfinite(x):
+        return float(f"{x:.{k}g}")
+    return x
+
+
+def summary(line):
+    """value (zone-updates/s), ms per step, predictor roofline fraction and
+    one-step errors of each form; status of the other workloads"""
+    out = {"fp64": {"v": _sig(line["value"]), "ms": _sig(line["ms_per_step"]),
+                    "frac": _sig(line["roofline"]["frac"]),
+                    "l1_oracle": _sig(line["config"].get("l1_vs_oracle_one_step"))}}
+    forms = line.get("forms") or {}
+    if "fp32_bulk" in forms:
+        f = forms["fp32_bulk"]
+        out["fp32"] = {"v": _sig(f["value"]), "ms": _sig(f["ms_per_step"]),
+                       "frac": _sig(f["predictor_frac_fp32_peak"]),
+                       "l1": _sig(f.get("rel_l1_vs_fp64_gpu_one_step")),
+                       "linf": _sig(f.get("rel_linf_vs_fp64_gpu_one_step"))}
+    for k in ("fp64_gated", "fp32_gated"):
+        if k in forms:
+            f = forms[k]
+            out[k] = {"v": _sig(f["value"]), "ms": _sig(f["ms_per_step"]),
+                      "flagged": _sig(f["flagged_fraction"]),
+                      "l1_full_weno": _sig(f.get("rel_l1_vs_full_weno_fp64_one_step"))}
+    for name, d in (line.get("other_workloads") or {}).items():
+        out[name.split("_")[0]] = {"v": _sig(d["value"]), "ms": _sig(d["ms_per_step"]),
+                                   "status": "ok" if d["status"] == "ok" else d["status"][:40]}
+    return out
 
 
 def run_reference(args, rank, world):

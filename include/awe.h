@@ -59,7 +59,11 @@ typedef enum {
   AWE_BC_REFLECT = 2,     /* mirror image, normal momentum negated */
   AWE_BC_INFLOW = 3,      /* fixed conserved state inflow[face] */
   AWE_BC_DMR_BOTTOM = 4,  /* inflow[face] for x < 1/6, reflecting wall beyond */
-  AWE_BC_DMR_TOP = 5      /* inflow[face] if x < 1/6 + (1 + 20 t)/sqrt(3), else pre */
+  AWE_BC_DMR_TOP = 5,     /* inflow[face] if x < 1/6 + (1 + 20 t)/sqrt(3), else pre */
+  AWE_BC_EXCHANGE = 6     /* ghost planes written by the caller with awe_halo_unpack
+                             (the neighbour subdomain's planes of a slab
+                             decomposition); allowed only on the two faces of the
+                             outermost dimension (z in 3D, y in 2D) */
 } awe_bc;
 
 /* Arithmetic forms of the step. */
@@ -122,6 +126,9 @@ typedef struct {
   int scheme;            /* awe_scheme: ADER (default) or SSP Runge-Kutta */
   int rk_stages;         /* AWE_SCHEME_SSPRK: 2, 3 or 5 stages (0: 2, 3, 5 at
                             orders 2, 3, 4, as in Table IV) */
+  double dx[3];          /* zone sizes; 0 = (hi - lo) / n.  A subdomain of a
+                            slab decomposition passes the undivided grid's, so
+                            that its updates round exactly as that grid's */
 } awe_config;
 
 /* Create a grid (allocates all device memory).  Cites: Fig. 1 data region.
@@ -169,6 +176,51 @@ int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out);
 int awe_step(awe_grid* g, double dt, double* dt_next_out);
 /* Synchronise and report a non-physical state flagged by earlier steps. */
 int awe_check(awe_grid* g);
+
+/* ---- slab decomposition (one subdomain per grid) ----
+ * The paper's code splits the domain into patches and, per time step,
+ * exchanges their ghost zones once and takes the MIN of dt over all of them
+ * (Sec. II.2, the MPI remarks after Fig. 7; Sec. V, the patch layer): ADER
+ * needs one exchange per step, a Runge-Kutta scheme one per stage (Sec. I.1).
+ * Here a subdomain is an ordinary grid whose faces towards its neighbours
+ * along the outermost dimension have AWE_BC_EXCHANGE.  Before each stage the
+ * caller packs the g = order planes next to each such face, moves them to the
+ * neighbour (device copy, NCCL, host) and unpacks the neighbour's planes into
+ * the ghost planes; the library fills every other ghost zone itself.
+ * Buffer layout: [var][plane][inner ghosted extent], planes ordered by
+ * increasing coordinate, inner extent (n_y + 2g)(n_x + 2g) in 3D, n_x + 2g in
+ * 2D, x fastest; a packed low-side buffer is the neighbour's high-side ghost
+ * content and vice versa.  With g = order ghost planes every zone that a
+ * subdomain reconstructs sees the same stencils as in the undivided grid, so
+ * the subdomains' steps together equal the undivided step bit for bit.  The
+ * gate is refused on such grids (AWE_ERR_ARG at awe_create): its flags need
+ * stencils beyond the ghost planes, and the two sides of an exchanged face
+ * would reconstruct the zones beside it differently. */
+/* Doubles in one halo buffer. */
+int awe_halo_size(const awe_grid* g, size_t* count);
+/* Pack the planes next to face `side` (0 = low, 1 = high) of the state that the
+ * next stage reads, with their inner-dimension ghost zones filled first (at
+ * the stage's boundary time).  on_device: 1 = device pointer (enqueued on the
+ * grid's stream), 0 = host pointer (synchronises). */
+int awe_halo_pack(awe_grid* g, int side, double* buf, int on_device);
+/* Write a neighbour's packed planes into the ghost planes beyond face `side` of
+ * the state that the next stage reads.  Same pointer conventions. */
+int awe_halo_unpack(awe_grid* g, int side, const double* buf, int on_device);
+/* Stages of one step: 1 for ADER, the Runge-Kutta stage count for SSPRK. */
+int awe_stage_count(const awe_grid* g, int* stages);
+/* Run stage k of the current step (k must be the next one: 0, 1, ...).
+ * Stage 0 takes dt as awe_step does (dt > 0, or the device-resident dt);
+ * the last stage finishes the step (t += dt, device dt = cfl / signal-speed
+ * max of this subdomain's updated state).  awe_step runs all stages at once
+ * and is refused (AWE_ERR_STATE) on a multi-stage grid with exchanged faces,
+ * whose ghosts must be exchanged between the stages. */
+int awe_stage(awe_grid* g, int k, double dt);
+/* The device-resident dt (the one awe_step(g, 0, ...) uses): read or write it
+ * through a host pointer (synchronises) or a device pointer (enqueued), so
+ * that the subdomains of a decomposition can take the minimum of their dt
+ * (= cfl / max of their signal speeds) without a host round trip. */
+int awe_get_dt(awe_grid* g, double* dt, int on_device);
+int awe_set_dt(awe_grid* g, const double* dt, int on_device);
 /* Number of box zones (active zones and one layer around them, per
  * reconstruction: once per step for ADER, once per stage for SSPRK) whose
  * face states went to the positivity fallback (cfg.fallback) since the last
@@ -265,9 +317,13 @@ int awe_mlp_forward(int nin, const float* params, const float* X, long B, float*
  * until the process exits, so grids above 268,435,456 zones are rejected
  * (AWE_ERR_ARG, message in awe_last_error(NULL)).  The first call on each
  * device looks up that array's device address; make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race and
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that destroys and re-creates the device's
+ * primary context) this entry point must not be called again in that
+ * process.  All calls share the array: calls that overlap on the GPU race and
  * must be serialised by the caller.  dt = 0 signals a non-physical or
- * non-finite zone. */
+ * non-finite zone.  U and dt are not checked for extent (the C ABI cannot
+ * see it): U must hold (dim + 2) * prod(n) doubles. */
 int awe_cfl_dt_noalloc(const double* U, int dim, const int* n, const double* dx, double gamma,
                        double cfl, double* dt, void* stream);
 

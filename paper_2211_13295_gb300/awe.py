@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libawe.so")
 
 AWE_OK, AWE_ERR_ARG, AWE_ERR_CUDA, AWE_ERR_OOM, AWE_ERR_NONPHYSICAL, AWE_ERR_TIMEOUT, AWE_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6
-BC = {"periodic": 0, "outflow": 1, "reflect": 2, "inflow": 3, "dmr_bottom": 4, "dmr_top": 5}
+BC = {"periodic": 0, "outflow": 1, "reflect": 2, "inflow": 3, "dmr_bottom": 4, "dmr_top": 5, "exchange": 6}
 PREC = {"fp64": 0, "fp32": 1}
 RIEMANN = {"hllc": 0, "hll": 1, "hllem": 2, "rusanov": 3}
 SCHEME = {"ader": 0, "ssprk": 1}
@@ -41,7 +41,7 @@ class AweConfig(C.Structure):
         ("inflow", (C.c_double * 5) * 6), ("pre", C.c_double * 5), ("prec", C.c_int),
         ("picard", C.c_int), ("weno_eps", C.c_double), ("lin", C.c_double * 4), ("cfl", C.c_double),
         ("gate", C.c_int), ("slab", C.c_int), ("fallback", C.c_int),
-        ("riemann", C.c_int), ("scheme", C.c_int), ("rk_stages", C.c_int),
+        ("riemann", C.c_int), ("scheme", C.c_int), ("rk_stages", C.c_int), ("dx", C.c_double * 3),
     ]
 
 
@@ -89,6 +89,13 @@ def lib():
         "awe_measure_fma_peaks": (C.c_int, [dp, dp]),
         "awe_cfl_dt_noalloc": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), dp, C.c_double, C.c_double,
                                          vp, vp]),
+        "awe_halo_size": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+        "awe_halo_pack": (C.c_int, [vp, C.c_int, vp, C.c_int]),
+        "awe_halo_unpack": (C.c_int, [vp, C.c_int, vp, C.c_int]),
+        "awe_stage_count": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "awe_stage": (C.c_int, [vp, C.c_int, C.c_double]),
+        "awe_get_dt": (C.c_int, [vp, vp, C.c_int]),
+        "awe_set_dt": (C.c_int, [vp, vp, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -106,7 +113,8 @@ def exported_symbols():
         "awe_probe_fluxes", "awe_profile", "awe_profile_count", "awe_profile_read", "awe_gate_dims",
         "awe_gate_set_weights", "awe_gate_features", "awe_gate_labels", "awe_gate_flags", "awe_gate_stats",
         "awe_mlp_train", "awe_mlp_loss_grad", "awe_mlp_forward", "awe_measure_fma_peaks",
-        "awe_cfl_dt_noalloc", "awe_fallback_count",
+        "awe_cfl_dt_noalloc", "awe_fallback_count", "awe_halo_size", "awe_halo_pack", "awe_halo_unpack",
+        "awe_stage_count", "awe_stage", "awe_get_dt", "awe_set_dt",
     ]
 
 
@@ -166,6 +174,8 @@ def make_config(prob, prec="fp64", gate=False, slab=0, cfl=None, picard=None) ->
     c.riemann = RIEMANN[getattr(prob, "riemann", "hllc")]
     c.scheme = SCHEME[getattr(prob, "scheme", "ader")]
     c.rk_stages = int(getattr(prob, "rk_stages", 0))
+    for d, h in enumerate(getattr(prob, "dxs", ()) or ()):
+        c.dx[d] = float(h)
     return c
 
 
@@ -237,6 +247,51 @@ class Grid:
 
     def check(self):
         _check(lib().awe_check(self.h), self.h)
+
+    # stages, halos and dt of a subdomain (slab decomposition) ------------
+    def stage_count(self):
+        n = C.c_int()
+        _check(lib().awe_stage_count(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def stage(self, k, dt=0.0):
+        _check(lib().awe_stage(self.h, int(k), float(dt)), self.h)
+
+    def halo_size(self):
+        n = C.c_size_t()
+        _check(lib().awe_halo_size(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def halo_pack(self, side, out):
+        """planes next to face `side` of the next stage's input into `out`
+        (numpy array or contiguous float64 tensor of halo_size() elements)"""
+        p, dev = _ptr(out)
+        _check(lib().awe_halo_pack(self.h, int(side), p, dev), self.h)
+        return out
+
+    def halo_unpack(self, side, buf):
+        p, dev = _ptr(buf)
+        _check(lib().awe_halo_unpack(self.h, int(side), p, dev), self.h)
+
+    def get_dt(self, out=None):
+        """device-resident dt: into `out` (a float64 tensor on the device, no
+        host round trip) or returned as a float"""
+        if out is None:
+            v = C.c_double()
+            _check(lib().awe_get_dt(self.h, C.byref(v), 0), self.h)
+            return v.value
+        p, dev = _ptr(out)
+        _check(lib().awe_get_dt(self.h, p, dev), self.h)
+        return out
+
+    def set_dt(self, dt):
+        """dt from a float or from a one-element float64 tensor on the device"""
+        if isinstance(dt, (int, float)):
+            v = C.c_double(float(dt))
+            _check(lib().awe_set_dt(self.h, C.byref(v), 0), self.h)
+        else:
+            p, dev = _ptr(dt)
+            _check(lib().awe_set_dt(self.h, p, dev), self.h)
 
     def fallback_count(self):
         """box zones sent to the positivity fallback since the last call"""
@@ -362,7 +417,29 @@ def measure_fma_peaks():
 
 def cfl_dt_noalloc(U, dim, n, dx, gamma, cfl, dt_out):
     """awe_cfl_dt_noalloc on CUDA tensors: U (state, float64, awe_get_state
-    layout) and dt_out (one float64) on the current device; enqueues only."""
+    layout) and dt_out (one float64) on the current device; enqueues only.
+
+    The C entry point cannot see the extent of the buffers it is given, so the
+    checks that keep its kernel inside them are made here, before the call."""
+    import torch
+    if dim not in (2, 3) or len(n) != dim or len(dx) != dim:
+        raise ValueError("cfl_dt_noalloc: dim must be 2 or 3, with dim entries in n and dx")
+    for name, t in (("U", U), ("dt_out", dt_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+            raise ValueError(f"cfl_dt_noalloc: {name} must be a float64 CUDA tensor")
+    dev = torch.cuda.current_device()
+    for name, t in (("U", U), ("dt_out", dt_out)):
+        if not t.is_contiguous() or t.device.index != dev:
+            raise ValueError(f"cfl_dt_noalloc: {name} must be contiguous and on the current device")
+    zones = 1
+    for v in n:
+        if int(v) < 1:
+            raise ValueError("cfl_dt_noalloc: zone counts must be positive")
+        zones *= int(v)
+    if U.numel() != (dim + 2) * zones:
+        raise ValueError(f"cfl_dt_noalloc: U has {U.numel()} elements, the grid needs {(dim + 2) * zones}")
+    if dt_out.numel() < 1:
+        raise ValueError("cfl_dt_noalloc: dt_out needs one element")
     nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
     dd = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
     rc = lib().awe_cfl_dt_noalloc(C.c_void_p(U.data_ptr()), dim, nn, dd, float(gamma), float(cfl),

@@ -66,6 +66,8 @@ struct awe_grid {
   double* stage = nullptr;  // state staging [nv][nact]
   double* Urk[2] = {nullptr, nullptr};  // Runge-Kutta stage states (ghosted)
   awe::RKScheme rk;
+  int next_stage = 0;       // stage of the current step that runs next (awe_stage)
+  double* halo_stage = nullptr;  // host-pointer halo transfers [halo_count]
   bool poison = false;  // AWE_POISON=1 at create: NaN-fill the intermediates before use
   long long szX = 0, szY = 0, szXY = 0, szW = 0, szFS = 0, szF = 0;
   void* ptab = nullptr;
@@ -95,6 +97,7 @@ int fail(awe_grid* g, int code, const std::string& msg) {
 
 int cuda_fail(awe_grid* g, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // a non-sticky error (a rejected argument) must not resurface in a later call
   return fail(g, e == cudaErrorMemoryAllocation ? AWE_ERR_OOM : AWE_ERR_CUDA, m);
 }
 
@@ -354,33 +357,90 @@ bool rk_plan(const RKScheme& r, RKPlan& p) {
   return true;
 }
 
-int rk_step(awe_grid* g) {
+double* rk_buffer(awe_grid* g, int b) { return b == -1 ? g->U[g->cur] : b == 2 ? g->U[1 - g->cur] : g->Urk[b]; }
+
+// Stage k of a Runge-Kutta step: reads the stage input buffer of the plan,
+// writes or accumulates into the stages it feeds.  An output stage starts
+// (init) at the first input stage that contributes to it.
+int rk_stage(awe_grid* g, int k) {
   const RKScheme& r = g->rk;
   RKPlan p;
   if (!rk_plan(r, p)) return fail(g, AWE_ERR_STATE, "Runge-Kutta stage plan");
-  auto bufp = [&](int b) { return b == -1 ? g->U[g->cur] : b == 2 ? g->U[1 - g->cur] : g->Urk[b]; };
   bool started[kRKMax + 1] = {false};
-  for (int k = 0; k < r.s; ++k) {
-    double* in = bufp(p.buf[k]);
-    fill_ghosts(g, in, r.c[k]);
-    const unsigned char* flags = gate_flags_for_step(g, in);
-    RKOut o[2];
-    for (int j = 0; j < p.nout[k]; ++j) {
-      int i = p.stage[k][j];
-      o[j].out = bufp(p.buf[i]);
-      o[j].init = started[i] ? 0 : 1;
-      o[j].a0 = r.alpha[i][0];
-      o[j].al = k == 0 ? 0.0 : r.alpha[i][k];
-      o[j].be = r.beta[i][k];
-      started[i] = true;
+  for (int kk = 0; kk < k; ++kk)
+    for (int j = 0; j < p.nout[kk]; ++j) started[p.stage[kk][j]] = true;
+  double* in = rk_buffer(g, p.buf[k]);
+  fill_ghosts(g, in, r.c[k]);
+  const unsigned char* flags = gate_flags_for_step(g, in);
+  RKOut o[2];
+  for (int j = 0; j < p.nout[k]; ++j) {
+    int i = p.stage[k][j];
+    o[j].out = rk_buffer(g, p.buf[i]);
+    o[j].init = started[i] ? 0 : 1;
+    o[j].a0 = r.alpha[i][0];
+    o[j].al = k == 0 ? 0.0 : r.alpha[i][k];
+    o[j].be = r.beta[i][k];
+  }
+  if (p.nout[k] < 2) o[1] = o[0];
+  for (int sidx = 0; sidx < nslabs(g); ++sidx) {
+    int z0, z1;
+    slab_range(g, sidx, z0, z1);
+    run_slab_rk(g, in, z0, z1, flags, o[0], o[1], p.nout[k], k == r.s - 1);
+  }
+  return AWE_OK;
+}
+
+int stage_count(const awe_grid* g) { return g->cfg.scheme == AWE_SCHEME_SSPRK ? g->rk.s : 1; }
+
+// the state buffer that stage k reads, and the time offset (in units of dt) of
+// its boundary values
+double* stage_input(awe_grid* g, int k, double* c) {
+  if (g->cfg.scheme != AWE_SCHEME_SSPRK) {
+    *c = 0.0;
+    return g->U[g->cur];
+  }
+  RKPlan p;
+  rk_plan(g->rk, p);
+  *c = g->rk.c[k];
+  return rk_buffer(g, p.buf[k]);
+}
+
+bool has_exchange(const awe_grid* g) {
+  const int od = g->q.dim - 1;
+  return g->q.bc[2 * od] == AWE_BC_EXCHANGE || g->q.bc[2 * od + 1] == AWE_BC_EXCHANGE;
+}
+
+// one stage of the current step (the caller checked k == g->next_stage)
+int run_stage(awe_grid* g, int k, double dt) {
+  if (g->cfg.gate && !g->gate.have_weights) return fail(g, AWE_ERR_STATE, "gate enabled without weights");
+  if (k == 0) {
+    if (g->poison) {
+      const size_t nbytesU = sizeof(double) * g->q.nv * g->q.ntot;
+      cudaMemsetAsync(g->U[1 - g->cur], 0xFF, nbytesU, g->s);
+      for (int b = 0; b < 2; ++b)
+        if (g->Urk[b]) cudaMemsetAsync(g->Urk[b], 0xFF, nbytesU, g->s);
     }
-    if (p.nout[k] < 2) o[1] = o[0];
+    if (dt > 0) launch_set_scalar(g->d_scal + 1, dt, g->s);
+  }
+  if (g->cfg.scheme == AWE_SCHEME_SSPRK) {
+    int rc = rk_stage(g, k);
+    if (rc != AWE_OK) return rc;
+  } else {
+    fill_ghosts(g);
+    const unsigned char* flags = gate_flags_for_step(g);
     for (int sidx = 0; sidx < nslabs(g); ++sidx) {
       int z0, z1;
       slab_range(g, sidx, z0, z1);
-      run_slab_rk(g, in, z0, z1, flags, o[0], o[1], p.nout[k], k == r.s - 1);
+      run_slab(g, z0, z1, true, true, flags);
     }
   }
+  g->next_stage = k + 1;
+  if (k == stage_count(g) - 1) {
+    launch_finalize(g->q, g->d_scal + 0, g->d_scal + 1, g->d_smax, 1, g->s);
+    g->cur = 1 - g->cur;
+    g->next_stage = 0;
+  }
+  CK(g, cudaGetLastError());
   return AWE_OK;
 }
 
@@ -404,9 +464,18 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   for (int d = 0; d < c.dim; ++d) {
     if (c.n[d] < c.order) return fail(nullptr, AWE_ERR_ARG, "each dimension needs at least order zones");
     if (!(c.hi[d] > c.lo[d])) return fail(nullptr, AWE_ERR_ARG, "empty domain");
+    if (c.dx[d] < 0.0 || c.dx[d] != c.dx[d]) return fail(nullptr, AWE_ERR_ARG, "negative zone size");
   }
-  for (int f = 0; f < 2 * c.dim; ++f)
-    if (c.bc[f] < 0 || c.bc[f] > AWE_BC_DMR_TOP) return fail(nullptr, AWE_ERR_ARG, "bad boundary condition");
+  for (int f = 0; f < 2 * c.dim; ++f) {
+    if (c.bc[f] < 0 || c.bc[f] > AWE_BC_EXCHANGE) return fail(nullptr, AWE_ERR_ARG, "bad boundary condition");
+    if (c.bc[f] == AWE_BC_EXCHANGE && f / 2 != c.dim - 1)
+      return fail(nullptr, AWE_ERR_ARG, "AWE_BC_EXCHANGE only on the faces of the outermost dimension");
+    // the gate's flag of a ghost zone needs a feature stencil and dilation
+    // reaching beyond the g ghost planes: the two subdomains beside an
+    // exchanged face would reconstruct its zones with different weights
+    if (c.bc[f] == AWE_BC_EXCHANGE && c.gate)
+      return fail(nullptr, AWE_ERR_ARG, "the gate cannot be combined with AWE_BC_EXCHANGE");
+  }
   if (!(c.gamma > 1.0)) return fail(nullptr, AWE_ERR_ARG, "gamma must exceed 1");
   if (c.picard < 0 || c.picard > 8) return fail(nullptr, AWE_ERR_ARG, "picard out of range");
   if (c.slab < 0) return fail(nullptr, AWE_ERR_ARG, "negative slab");
@@ -436,7 +505,7 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
     bool act = d < c.dim;
     q.n[d] = act ? c.n[d] : 1;
     q.G[d] = act ? c.n[d] + 2 * q.g : 1;
-    q.dx[d] = act ? (c.hi[d] - c.lo[d]) / c.n[d] : 1.0;
+    q.dx[d] = act ? (c.dx[d] > 0.0 ? c.dx[d] : (c.hi[d] - c.lo[d]) / c.n[d]) : 1.0;
     q.lo[d] = act ? c.lo[d] : 0.0;
   }
   q.ntot = (long long)q.G[0] * q.G[1] * q.G[2];
@@ -520,6 +589,7 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
       {&g->FS, g->bytesT * sz.FS, "face states"},
       {&g->F, g->bytesT * sz.F, "fluxes"},
       {(void**)&g->stage, sizeof(double) * q.nv * nactive(q), "staging"},
+      {(void**)&g->halo_stage, sizeof(double) * halo_count(q), "halo staging"},
   };
   if (c.scheme == AWE_SCHEME_SSPRK) {
     allocs.push_back({(void**)&g->Urk[0], nbytesU, "Runge-Kutta stage state"});
@@ -578,7 +648,7 @@ int awe_destroy(awe_grid* g) {
   cudaStreamSynchronize(g->s);
   void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax,  g->d_err,  g->X,    g->Y,
                   g->XY,   g->W,    g->FS,     g->F,      g->stage,  g->ptab, g->Urk[0],
-                  g->Urk[1], g->d_fb};
+                  g->Urk[1], g->d_fb, g->halo_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   awe::gate_free(g->gate);
@@ -593,7 +663,7 @@ int awe_destroy(awe_grid* g) {
 // first transfer after an idle period of about a second costs tens of
 // milliseconds on this platform.  Anything else (pageable memory) goes through
 // the staging buffer with cudaMemcpyAsync.
-static bool host_mapped(const void* p) {
+static bool host_mapped_at(const void* p) {
   // only memory that the CUDA runtime itself page-locked (cudaHostAlloc or
   // cudaHostRegister): on platforms that address pageable memory from the
   // GPU the pointer attributes alone do not tell pinned memory apart
@@ -610,12 +680,22 @@ static bool host_mapped(const void* p) {
   return a.type == cudaMemoryTypeHost && a.devicePointer == p;
 }
 
+// the whole buffer [p, p + bytes): its first and its last element must both be
+// page-locked and mapped (a buffer registered over only part of its length,
+// such as a view into a larger registration's start, takes the staged copy)
+static bool host_mapped(const void* p, size_t bytes) {
+  if (!host_mapped_at(p)) return false;
+  if (bytes <= sizeof(double)) return true;
+  const char* last = static_cast<const char*>(p) + bytes - sizeof(double);
+  return host_mapped_at(last);
+}
+
 int awe_set_state(awe_grid* g, const double* U, int on_device) {
   if (!g || !U) return fail(g, AWE_ERR_ARG, "null argument");
   const Geo& q = g->q;
   long long n = nactive(q) * q.nv;
   const double* src = U;
-  if (!on_device && !host_mapped(U)) {
+  if (!on_device && !host_mapped(U, sizeof(double) * n)) {
     CK(g, cudaMemcpyAsync(g->stage, U, sizeof(double) * n, cudaMemcpyHostToDevice, g->s));
     src = g->stage;
   }
@@ -630,7 +710,7 @@ int awe_get_state(awe_grid* g, double* U, int on_device) {
   if (!g || !U) return fail(g, AWE_ERR_ARG, "null argument");
   const Geo& q = g->q;
   long long n = nactive(q) * q.nv;
-  const bool mapped = !on_device && host_mapped(U);
+  const bool mapped = !on_device && host_mapped(U, sizeof(double) * n);
   double* dst = on_device || mapped ? U : g->stage;
   int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
   k_gather<<<blocks, 256, 0, g->s>>>(q, g->U[g->cur], dst);
@@ -675,32 +755,84 @@ int awe_cfl_dt(awe_grid* g, double cfl, double* dt_out) {
 
 int awe_step(awe_grid* g, double dt, double* dt_next_out) {
   if (!g) return AWE_ERR_ARG;
-  if (g->cfg.gate && !g->gate.have_weights) return fail(g, AWE_ERR_STATE, "gate enabled without weights");
-  if (g->poison) {
-    const size_t nbytesU = sizeof(double) * g->q.nv * g->q.ntot;
-    cudaMemsetAsync(g->U[1 - g->cur], 0xFF, nbytesU, g->s);
-    for (int b = 0; b < 2; ++b)
-      if (g->Urk[b]) cudaMemsetAsync(g->Urk[b], 0xFF, nbytesU, g->s);
-  }
-  if (dt > 0) launch_set_scalar(g->d_scal + 1, dt, g->s);
-  if (g->cfg.scheme == AWE_SCHEME_SSPRK) {
-    int rc = rk_step(g);
+  if (g->next_stage != 0) return fail(g, AWE_ERR_STATE, "a step is in progress (awe_stage)");
+  if (stage_count(g) > 1 && has_exchange(g))
+    return fail(g, AWE_ERR_STATE, "exchanged faces need an exchange before every stage: use awe_stage");
+  for (int k = 0; k < stage_count(g); ++k) {
+    int rc = run_stage(g, k, dt);
     if (rc != AWE_OK) return rc;
-  } else {
-    fill_ghosts(g);
-    const unsigned char* flags = gate_flags_for_step(g);
-    for (int sidx = 0; sidx < nslabs(g); ++sidx) {
-      int z0, z1;
-      slab_range(g, sidx, z0, z1);
-      run_slab(g, z0, z1, true, true, flags);
-    }
   }
-  launch_finalize(g->q, g->d_scal + 0, g->d_scal + 1, g->d_smax, 1, g->s);
-  g->cur = 1 - g->cur;
-  CK(g, cudaGetLastError());
   if (dt_next_out) {
     CK(g, cudaMemcpyAsync(dt_next_out, g->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, g->s));
     return awe_check(g);
+  }
+  return AWE_OK;
+}
+
+int awe_stage_count(const awe_grid* g, int* stages) {
+  if (!g || !stages) return AWE_ERR_ARG;
+  *stages = stage_count(g);
+  return AWE_OK;
+}
+
+int awe_stage(awe_grid* g, int k, double dt) {
+  if (!g) return AWE_ERR_ARG;
+  if (k != g->next_stage) return fail(g, AWE_ERR_STATE, "stages run in order: 0, 1, ...");
+  return run_stage(g, k, dt);
+}
+
+int awe_halo_size(const awe_grid* g, size_t* count) {
+  if (!g || !count) return AWE_ERR_ARG;
+  *count = (size_t)halo_count(g->q);
+  return AWE_OK;
+}
+
+int awe_halo_pack(awe_grid* g, int side, double* buf, int on_device) {
+  if (!g || !buf || (side != 0 && side != 1)) return fail(g, AWE_ERR_ARG, "bad argument");
+  double c = 0.0;
+  double* in = stage_input(g, g->next_stage, &c);
+  // inner-dimension ghosts of the packed planes, at the stage's boundary time
+  fill_ghosts(g, in, c);
+  launch_halo(g->q, in, side, on_device ? buf : g->halo_stage, true, g->s);
+  CK(g, cudaGetLastError());
+  if (!on_device) {
+    CK(g, cudaMemcpyAsync(buf, g->halo_stage, sizeof(double) * halo_count(g->q), cudaMemcpyDeviceToHost, g->s));
+    CK(g, cudaStreamSynchronize(g->s));
+  }
+  return AWE_OK;
+}
+
+int awe_halo_unpack(awe_grid* g, int side, const double* buf, int on_device) {
+  if (!g || !buf || (side != 0 && side != 1)) return fail(g, AWE_ERR_ARG, "bad argument");
+  double c = 0.0;
+  double* out = stage_input(g, g->next_stage, &c);
+  const double* src = buf;
+  if (!on_device) {
+    CK(g, cudaMemcpyAsync(g->halo_stage, buf, sizeof(double) * halo_count(g->q), cudaMemcpyHostToDevice, g->s));
+    src = g->halo_stage;
+  }
+  launch_halo(g->q, out, side, const_cast<double*>(src), false, g->s);
+  CK(g, cudaGetLastError());
+  if (!on_device) CK(g, cudaStreamSynchronize(g->s));
+  return AWE_OK;
+}
+
+int awe_get_dt(awe_grid* g, double* dt, int on_device) {
+  if (!g || !dt) return fail(g, AWE_ERR_ARG, "null argument");
+  CK(g, cudaMemcpyAsync(dt, g->d_scal + 1, sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        g->s));
+  if (!on_device) CK(g, cudaStreamSynchronize(g->s));
+  return AWE_OK;
+}
+
+int awe_set_dt(awe_grid* g, const double* dt, int on_device) {
+  if (!g || !dt) return fail(g, AWE_ERR_ARG, "null argument");
+  if (on_device) {
+    CK(g, cudaMemcpyAsync(g->d_scal + 1, dt, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  } else {
+    if (!(*dt > 0)) return fail(g, AWE_ERR_ARG, "dt must be positive");
+    launch_set_scalar(g->d_scal + 1, *dt, g->s);
+    CK(g, cudaGetLastError());
   }
   return AWE_OK;
 }

@@ -29,12 +29,18 @@ __global__ void k_fill_ghosts(Geo q, double* __restrict__ U, const double* __res
     for (int v = 0; v < q.nv; ++v) sign[v] = 1.0;
     const double* fixed = nullptr;
     const double xc = q.lo[0] + (idx[0] + 0.5) * q.dx[0];
-    for (int d = q.dim - 1; d >= 0 && !fixed; --d) {
+    bool external = false;
+    for (int d = q.dim - 1; d >= 0 && !fixed && !external; --d) {
       if (idx[d] >= 0 && idx[d] < q.n[d]) continue;
       int side = idx[d] < 0 ? 0 : 1;
       int bc = q.bc[2 * d + side];
       if (bc == AWE_BC_DMR_BOTTOM) bc = (xc < 1.0 / 6.0) ? AWE_BC_INFLOW : AWE_BC_REFLECT;
       switch (bc) {
+        case AWE_BC_EXCHANGE:
+          // a neighbour's plane, written by awe_halo_unpack (only on the
+          // outermost dimension, which this loop resolves first)
+          external = true;
+          break;
         case AWE_BC_PERIODIC: {
           int m = idx[d] % q.n[d];
           idx[d] = m < 0 ? m + q.n[d] : m;
@@ -59,6 +65,7 @@ __global__ void k_fill_ghosts(Geo q, double* __restrict__ U, const double* __res
           fixed = q.pre;
       }
     }
+    if (external) continue;
     if (fixed) {
       for (int v = 0; v < q.nv; ++v) U[v * q.ntot + z] = sign[v] * fixed[v];
     } else {
@@ -75,6 +82,53 @@ void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, const double
   long long blocks = (total + threads - 1) / threads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_fill_ghosts<<<(int)blocks, threads, 0, s>>>(q, U, d_t, d_dt, c);
+}
+
+// Halo planes of the outermost dimension od (z in 3D, y in 2D) for a slab
+// decomposition: buffer [var][plane p][inner ghosted extent].  Pack reads the
+// active planes p (low side) or n - g + p (high side); unpack writes the ghost
+// planes -g + p (low) or n + p (high), in active coordinates.  The ghosted
+// index of plane k along od times the inner extent is the offset of its first
+// zone, because od is the slowest dimension of the layout.
+__global__ void k_halo_pack(Geo q, const double* __restrict__ U, int side, double* __restrict__ buf) {
+  const int od = q.dim - 1;
+  const long long plane = od == 2 ? (long long)q.G[0] * q.G[1] : (long long)q.G[0];
+  const long long per_v = (long long)q.g * plane;
+  const long long n = (long long)q.nv * per_v;
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < n;
+       z += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(z / per_v);
+    const long long rem = z - v * per_v;
+    const int p = (int)(rem / plane);
+    const long long o = rem - p * plane;
+    const int k = (side ? q.n[od] - q.g + p : p) + q.g;  // ghosted index along od
+    buf[z] = U[v * q.ntot + k * plane + o];
+  }
+}
+__global__ void k_halo_unpack(Geo q, double* __restrict__ U, int side, const double* __restrict__ buf) {
+  const int od = q.dim - 1;
+  const long long plane = od == 2 ? (long long)q.G[0] * q.G[1] : (long long)q.G[0];
+  const long long per_v = (long long)q.g * plane;
+  const long long n = (long long)q.nv * per_v;
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < n;
+       z += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(z / per_v);
+    const long long rem = z - v * per_v;
+    const int p = (int)(rem / plane);
+    const long long o = rem - p * plane;
+    const int k = side ? q.n[od] + q.g + p : p;  // ghosted index along od
+    U[v * q.ntot + k * plane + o] = buf[z];
+  }
+}
+long long halo_count(const Geo& q) {
+  const long long plane = q.dim == 3 ? (long long)q.G[0] * q.G[1] : (long long)q.G[0];
+  return (long long)q.nv * q.g * plane;
+}
+void launch_halo(const Geo& q, double* U, int side, double* buf, bool pack, cudaStream_t s) {
+  long long blocks = (halo_count(q) + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (pack) k_halo_pack<<<(int)blocks, 256, 0, s>>>(q, U, side, buf);
+  else k_halo_unpack<<<(int)blocks, 256, 0, s>>>(q, U, side, buf);
 }
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }

@@ -505,6 +505,8 @@ struct Bufs;  // defined in awe_api.cu
 void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, const double* d_dt, double c,
                         cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
+long long halo_count(const Geo& q);
+void launch_halo(const Geo& q, double* U, int side, double* buf, bool pack, cudaStream_t s);
 void launch_signal_max(const Geo& q, const double* U, unsigned long long* smax, int* err,
                        cudaStream_t s);
 void launch_finalize(const Geo& q, double* d_t, double* d_dt, unsigned long long* smax,

@@ -232,3 +232,17 @@ def predictor_flops_per_launch(prob, picard=None):
     n = [prob.n[d] if d < D else 1 for d in range(3)]
     box = (n[0] + 2) * (n[1] + 2) * (n[2] + 2 if D == 3 else 1)
     return predictor_flops(D, N, picard)[0] * box
+
+
+def predictor_source_sha():
+    """Short hash of the predictor kernel's sources: a DRAM-traffic figure
+    measured by ncu on one version of the kernel is only reported while the
+    sources it was measured on are unchanged."""
+    import hashlib
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    h = hashlib.sha256()
+    for name in ("awe_predict.cu", "predict_index.cuh", "awe_internal.cuh"):
+        with open(os.path.join(here, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]

@@ -56,6 +56,7 @@ class Problem:
     scheme: str = "ader"                 # time stepping: ader, or ssprk (Table IV's comparison)
     rk_stages: int = 0                   # SSP-RK stages (2, 3, 5); 0: 2, 3, 5 at orders 2, 3, 4
     params: dict = dataclasses.field(default_factory=dict)
+    dxs: tuple = ()                      # zone sizes, if not (hi - lo) / n (subdomains)
 
     def __post_init__(self):
         if not self.lin:
@@ -73,6 +74,8 @@ class Problem:
         return int(np.prod(self.n[: self.dim]))
 
     def dx(self, d):
+        if self.dxs:
+            return self.dxs[d]
         return (self.hi[d] - self.lo[d]) / self.n[d]
 
     def shape(self):
@@ -187,9 +190,13 @@ def _sod_ic(prob):
 # ---------------------------------------------------------------------------
 # 3D Taylor-Green vortex (exact zone averages: separable products)
 # ---------------------------------------------------------------------------
-def tgv3d(n=256, order=4, cfl=0.3, steps=100) -> Problem:
+def tgv3d(n=256, order=4, cfl=0.3, steps=100, nz=None) -> Problem:
+    """Taylor-Green vortex on [0, 2 pi]^3 with n^3 zones; nz > n stacks nz / n
+    periods along z (the same zone size), the grid of a z-slab decomposition
+    that gives every rank an n^3 slab."""
     L = 2.0 * math.pi
-    return Problem("tgv3d", 3, (n, n, n), (0.0, 0.0, 0.0), (L, L, L), order, cfl=cfl, steps=steps)
+    nz = n if nz is None else nz
+    return Problem("tgv3d", 3, (n, n, nz), (0.0, 0.0, 0.0), (L, L, L * nz / n), order, cfl=cfl, steps=steps)
 
 
 def _avg_trig(c, h, kind, k=1.0):

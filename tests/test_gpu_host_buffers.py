@@ -84,3 +84,47 @@ def test_large_fresh_pageable_buffers_read_the_grid_state(awe, prec):
     if prec == "fp32":
         d = np.abs(reads["fp32"] - reads["fp64"]).max()
         assert 0 < d < 1e-3
+
+
+def test_partly_registered_buffers_are_never_read_directly(awe):
+    """A host buffer page-locked over only its first pages (cudaHostRegister of
+    a prefix) must not be read or written by the scatter/gather kernels (both
+    ends of the buffer are checked).  The staged copy of such a range is
+    refused by CUDA itself (invalid argument): the call must either move the
+    state bit for bit or fail with AWE_ERR_CUDA, and the grid must stay
+    usable either way."""
+    import torch
+    cudart = torch.cuda.cudart()
+    prob = P.tgv3d(n=32, order=4, cfl=0.3)
+    U = np.ascontiguousarray(prob.initial_state())
+    prefix = 1 << 16  # 64 KB of a 1.3 MB state
+    src = np.empty_like(U)
+    src[...] = U
+    dst = np.full_like(U, 7.0)
+    g = awe.Grid(prob)
+    regs = []
+    try:
+        for buf in (src, dst):
+            assert int(cudart.cudaHostRegister(buf.ctypes.data, prefix, 0)) == 0
+            regs.append(buf)
+        for call, args in ((g.set_state, (src,)), (g.get_state, (dst,))):
+            try:
+                call(*args)
+            except awe.AweError as e:
+                assert e.code == awe.AWE_ERR_CUDA, e
+        if not np.array_equal(dst, np.full_like(U, 7.0)):
+            assert np.array_equal(dst, U)  # a transfer that happened was exact
+    finally:
+        for buf in regs:
+            cudart.cudaHostUnregister(buf.ctypes.data)
+    # the grid works on after the refused copies
+    g.set_state(U)
+    dt = g.cfl_dt()
+    g.step(dt)
+    a = g.get_state()
+    g.close()
+    h = awe.Grid(prob)
+    h.set_state(U)
+    h.step(dt)
+    assert np.array_equal(a, h.get_state())
+    h.close()
