@@ -617,8 +617,9 @@ def run_native(args, rank, world, local):
                        "l1_vs_oracle_one_step": parity},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
-                         "kernel": f"predictor ({'k_predict_fact' if prob.order == 4 else 'k_predict_direct'}"
-                                   f"<{'double' if args.form == 'fp64' else 'float'}>)",
+                         "kernel": "predictor (" + ("k_predict_direct" if prob.order != 4 else
+                                                    "k_predict_fact<double>" if args.form == "fp64" else
+                                                    "k_predict_lines (FP32)") + ")",
                          "peak_source": f"derived: 152 SMs x {'2 FP64' if args.form == 'fp64' else '128 FP32'} FMA/clk x 2 x 2.07 GHz",
                          "algorithmic_flops_per_launch": flops_pred, "avg_launch_ms": avg_pred,
                          "hbm": hbm_line},

@@ -588,6 +588,121 @@ __device__ __forceinline__ void store_node_y1(T* Y1, int s, const NodeAcc<T>& ac
     for (int e = 0; e < 3; ++e) Y1[(r * 64 + s) * 3 + e] = acc.a[r][e];
 }
 
+// Face states of one zone (whole warp): the time integral of G at the two face
+// time points (shared by all directions), then per (direction, side, variable)
+// the normal axis at +-1/2 and the two transverse axes at the face Gauss
+// points, the positivity fallback and the store.  sg holds G with rows GS
+// entries apart; scratch takes 340 entries.
+template <typename T, int GS>
+__device__ __forceinline__ void fact_face_states(const Geo& q, const T* sw, const T* sg, T* scratch,
+                                                 const Tabs<T>& tb, int lane, T gm1, long long nb, long long r,
+                                                 T* __restrict__ FS) {
+  // face states into shared memory.  Factorised evaluation: the time
+  // integral of G at the two face time points (shared by all directions),
+  // then per (direction, side, variable) the normal axis at +-1/2 and the two
+  // transverse axes at the face Gauss points.  Row = (d*2+side)*8 + q with
+  // q = i1 + 2*(i2 + 2*it), as the probes document.
+  T* fv = scratch;                      // [48][5] face values
+  T* gt = fv + 240;                     // [v][it][tri] time-integrated G, 100
+  for (int it = lane; it < 100; it += 32) {
+    int tr = it % 10, rest = it / 10, tq = rest % 2, v = rest / 2;
+    const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
+    T acc = T(0);
+    for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * GS + gm_fast(a, b, c, e)], tb.ITF[e][tq], acc);
+    gt[it] = acc;
+  }
+  __syncwarp();
+  if (lane < 30) {
+    const int v = lane % 5, ds = lane / 5, d = ds >> 1, side = ds & 1;
+    // axes: n = d (normal), t1 < t2 the transverse ones.  Every loop below
+    // is unrolled over compile-time exponents; the mode index of (an on the
+    // normal axis, p1 on t1, p2 on t2) is one of three constants, picked by d
+    // w part: contract the normal axis at the face, then t1, then t2
+    T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index p3idx(p1, p2)
+#pragma unroll
+    for (int p2 = 0; p2 <= 3; ++p2)
+#pragma unroll
+      for (int p1 = 0; p1 <= 3 - p2; ++p1) {
+        T acc = T(0);
+#pragma unroll
+        for (int an = 0; an <= 3 - p1 - p2; ++an) {
+          const int m = d == 0 ? simplex_idx(3, an, p1, p2) : d == 1 ? simplex_idx(3, p1, an, p2)
+                                                                    : simplex_idx(3, p1, p2, an);
+          acc = fma(sw[v * 20 + m], tb.PE[an][side], acc);
+        }
+        wn2[p3idx(p1, p2)] = acc;
+      }
+    T w3[2][4];  // [i1][p2]
+#pragma unroll
+    for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+      for (int p2 = 0; p2 < 4; ++p2) {
+        T acc = T(0);
+#pragma unroll
+        for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[p3idx(p1, p2)], tb.PF[p1][i1], acc);
+        w3[i1][p2] = acc;
+      }
+    // G part per face time point
+    T gv[2][2][2];  // [it][i1][i2]
+#pragma unroll
+    for (int tq = 0; tq < 2; ++tq) {
+      const T* gtv = gt + (v * 2 + tq) * 10;
+      T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index p2idx(p1, p2)
+#pragma unroll
+      for (int p2 = 0; p2 <= 2; ++p2)
+#pragma unroll
+        for (int p1 = 0; p1 <= 2 - p2; ++p1) {
+          T acc = T(0);
+#pragma unroll
+          for (int an = 0; an <= 2 - p1 - p2; ++an) {
+            const int m = d == 0 ? tri2idx(an, p1, p2) : d == 1 ? tri2idx(p1, an, p2) : tri2idx(p1, p2, an);
+            acc = fma(gtv[m], tb.PE[an][side], acc);
+          }
+          gn2[p2idx(p1, p2)] = acc;
+        }
+#pragma unroll
+      for (int i1 = 0; i1 < 2; ++i1) {
+        T g3[3];
+#pragma unroll
+        for (int p2 = 0; p2 < 3; ++p2) {
+          T acc = T(0);
+#pragma unroll
+          for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[p2idx(p1, p2)], tb.PF[p1][i1], acc);
+          g3[p2] = acc;
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < 2; ++i2) {
+          T acc = T(0);
+#pragma unroll
+          for (int p2 = 0; p2 < 3; ++p2) acc = fma(g3[p2], tb.PF[p2][i2], acc);
+          gv[tq][i1][i2] = acc;
+        }
+      }
+    }
+#pragma unroll
+    for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+      for (int i2 = 0; i2 < 2; ++i2) {
+        T acc = T(0);
+#pragma unroll
+        for (int p2 = 0; p2 < 4; ++p2) acc = fma(w3[i1][p2], tb.PF[p2][i2], acc);
+#pragma unroll
+        for (int tq = 0; tq < 2; ++tq) fv[(ds * 8 + i1 + 2 * (i2 + 2 * tq)) * 5 + v] = acc - gv[tq][i1][i2];
+      }
+  }
+  __syncwarp();
+  bool bad = false;
+  if (q.fallback)
+    for (int row = lane; row < 48; row += 32) bad = bad || !state_physical5<T>(fv + row * 5, gm1);
+  bad = __any_sync(0xffffffffu, bad) && q.fallback;
+  if (bad && lane == 0 && q.fb_count) atomicAdd(q.fb_count, 1ULL);
+  __syncwarp();
+  for (int it = lane; it < 240; it += 32) {
+    int v = it % 5, row = it / 5;
+    FS[((long long)row * 5 + v) * nb + r] = bad ? sw[v * 20] : fv[row * 5 + v];
+  }
+}
+
 // Register budgets: FP32 at 8 blocks of two zone-warps per SM (its shared
 // memory allows 8); FP64 at most ~170 registers (its shared memory allows 4
 // blocks; more registers measured slower)
@@ -871,111 +986,414 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 8 : 6) k_predict_fa
       __syncwarp();
       fact_project<T, 2>(z, tb, ix, lane, lam);
     }
-    // face states into shared memory.  Factorised evaluation: the time
-    // integral of G at the two face time points (shared by all directions),
-    // then per (direction, side, variable) the normal axis at +-1/2 and the two
-    // transverse axes at the face Gauss points.  Row = (d*2+side)*8 + q with
-    // q = i1 + 2*(i2 + 2*it), as the probes document.
-    T* fv = z + FactSmem<T>::R1;          // [48][5] face values
-    T* gt = fv + 240;                     // [v][it][tri] time-integrated G, 100
-    for (int it = lane; it < 100; it += 32) {
-      int tr = it % 10, rest = it / 10, tq = rest % 2, v = rest / 2;
-      const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
-      T acc = T(0);
-      for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * 15 + gm_fast(a, b, c, e)], tb.ITF[e][tq], acc);
-      gt[it] = acc;
-    }
+    fact_face_states<T, 15>(q, sw, sg, z + FactSmem<T>::R1, tb, lane, gm1, nb, r, FS);
     __syncwarp();
-    if (lane < 30) {
-      const int v = lane % 5, ds = lane / 5, d = ds >> 1, side = ds & 1;
-      // axes: n = d (normal), t1 < t2 the transverse ones.  Every loop below
-      // is unrolled over compile-time exponents; the mode index of (an on the
-      // normal axis, p1 on t1, p2 on t2) is one of three constants, picked by d
-      // w part: contract the normal axis at the face, then t1, then t2
-      T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index p3idx(p1, p2)
-#pragma unroll
-      for (int p2 = 0; p2 <= 3; ++p2)
-#pragma unroll
-        for (int p1 = 0; p1 <= 3 - p2; ++p1) {
-          T acc = T(0);
-#pragma unroll
-          for (int an = 0; an <= 3 - p1 - p2; ++an) {
-            const int m = d == 0 ? simplex_idx(3, an, p1, p2) : d == 1 ? simplex_idx(3, p1, an, p2)
-                                                                      : simplex_idx(3, p1, p2, an);
-            acc = fma(sw[v * 20 + m], tb.PE[an][side], acc);
-          }
-          wn2[p3idx(p1, p2)] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 predictor, 3D, N = 3, with node lines in registers
+// ---------------------------------------------------------------------------
+// The FP32 form of the factorised kernel above is bound by shared-memory
+// bandwidth: every contraction stage reads its operands from shared memory
+// for one FMA each.  Here a zone takes 16 lanes (two zones per warp) and each
+// lane owns one line of four nodes along z, (x_i, y_j, z_k), k = 0..3.  The
+// evaluation of the Picard iterate at the line's 16 space-time points, the
+// fluxes, their time contraction and the first projection step (along z)
+// happen in the lane's registers; only the z-projected fluxes go through
+// shared memory to the two remaining projection steps.
+//
+// Row sets at the nodes (NodeAcc order): 0..2 the diagonal momentum flux of
+// direction r, 3..5 the off-diagonal rho v_a v_b of (0,1), (0,2), (1,2), 6..8
+// the energy flux of direction r - 6.  The z step keeps, per row, the pairs
+// (p, e) of z-mode and time mode in nine slots with the same positions in
+// every row:
+//   slot  0     1     2     3     4     5     6     7     8
+//   (p,e) (1,0) (1,1) (2,0) (0,0) (0,1) (0,2) (3,0) (2,1) (1,2)
+// Slots 0-5 (p + e <= 2) serve the directions x and y, for which z is a plain
+// axis; slots 0-2 and 6-8 (p >= 1, p + e <= 3) serve direction z, whose
+// derivative is applied to the projection coefficients afterwards
+// (dP1 = P0, dP2 = 2 P1, dP3 = 3 P2 + P0/10).  The second step contracts one
+// plain axis in three rounds, each for the four variables 1..4:
+//   round 0: direction x, contract y over slots 0-5  (rows 0, 3, 4, 6)
+//   round 1: direction y, contract x over slots 0-5  (rows 3, 1, 5, 7)
+//   round 2: direction z, contract y over slots 0-2, 6-8 (rows 4, 5, 2, 8)
+// and the last step contracts the remaining axis: with the derivative
+// factors QN in rounds 0 and 1 (the same operator as the factorised kernel),
+// with the plain basis followed by the modal derivative in round 2.
+__host__ __device__ constexpr int ln_p(int s) {
+  return s == 0 || s == 1 || s == 8 ? 1 : s == 2 || s == 7 ? 2 : s == 6 ? 3 : 0;
+}
+__host__ __device__ constexpr int ln_e(int s) { return s == 1 || s == 4 || s == 7 ? 1 : s == 5 || s == 8 ? 2 : 0; }
+__host__ __device__ constexpr bool ln_row_xy(int r) { return r != 2 && r != 8; }            // serves x or y
+__host__ __device__ constexpr bool ln_row_z(int r) { return r == 2 || r == 4 || r == 5 || r == 8; }  // serves z
+__host__ __device__ constexpr bool ln_used(int r, int s) { return s < 3 || (s < 6 ? ln_row_xy(r) : ln_row_z(r)); }
+// the slots of round R (index u = 0..5)
+__host__ __device__ constexpr int ln_round_slot(int R, int u) { return R == 2 && u >= 3 ? u + 3 : u; }
+// largest mode of the contracted axis kept for slot s in round R (the total
+// degree of the projection: <= 2 for a plain z axis, <= 3 for z's own)
+__host__ __device__ constexpr int ln_qmax(int R, int s) { return (R == 2 ? 3 : 2) - ln_p(s) - ln_e(s); }
+// position of (slot index u, mode q) among the 10 outputs of a round
+__host__ __device__ constexpr int ln_tri(int R, int u, int q) {
+  int t = 0;
+  for (int uu = 0; uu < u; ++uu) t += ln_qmax(R, ln_round_slot(R, uu)) + 1;
+  return t + q;
+}
+// row of round R for variable 1 + vv (packed: 4 bits per entry)
+__host__ __device__ constexpr int ln_round_row(int R, int vv) {
+  return R == 0 ? (vv == 0 ? 0 : vv == 1 ? 3 : vv == 2 ? 4 : 6)
+       : R == 1 ? (vv == 0 ? 3 : vv == 1 ? 1 : vv == 2 ? 5 : 7)
+                : (vv == 0 ? 4 : vv == 1 ? 5 : vv == 2 ? 2 : 8);
+}
+// Shared-memory base of each row of the z-projected fluxes (16 floats per
+// slot): rows 160 floats apart, offset by 4 * beta(r) floats so that the four
+// rows of every round start in four different groups of four banks
+// (beta = 0 2 1 1 2 0 3 3 3 gives each round four distinct values).
+__host__ __device__ constexpr int ln_beta(int r) {
+  return r == 0 || r == 5 ? 0 : r == 2 || r == 3 ? 1 : r == 1 || r == 4 ? 2 : 3;
+}
+__host__ __device__ constexpr int ln_rowbase(int r) { return 160 * r + 4 * ln_beta(r); }
+__host__ __device__ constexpr unsigned long long ln_pack_rowbase(int R) {
+  unsigned long long k = 0;
+  for (int vv = 0; vv < 4; ++vv) k |= (unsigned long long)ln_rowbase(ln_round_row(R, vv)) << (16 * vv);
+  return k;
+}
+// per G-mode b (15 modes, gmidx order), packed 4 bits per mode: the output
+// positions that the last step reads (rounds 0, 1: slot of (c, e) and the mode
+// of the contracted axis; round 2: slot of (c + 1, e)) and the slack of the
+// derivative factors
+__host__ __device__ constexpr int ln_plain_slot(int c, int e) {   // (c, e), c + e <= 2
+  return c == 1 ? (e == 0 ? 0 : 1) : c == 2 ? 2 : 3 + e;
+}
+__host__ __device__ constexpr int ln_z_u(int c, int e) {          // round-2 index of (c, e), c >= 1
+  return c == 1 ? (e == 0 ? 0 : e == 1 ? 1 : 5) : c == 2 ? (e == 0 ? 2 : 4) : 3;
+}
+__host__ __device__ constexpr int ln_gm_exp(int b, int k) {
+  int i = 0;
+  for (int e = 0; e <= 2; ++e)
+    for (int c = 0; c <= 2 - e; ++c)
+      for (int bb = 0; bb <= 2 - e - c; ++bb)
+        for (int a = 0; a <= 2 - e - bb - c; ++a) {
+          if (i == b) return k == 0 ? a : k == 1 ? bb : k == 2 ? c : e;
+          ++i;
         }
-      T w3[2][4];  // [i1][p2]
+  return 0;
+}
+__host__ __device__ constexpr unsigned long long ln_pack_gm(int which) {
+  unsigned long long k = 0;
+  for (int b = 0; b < 15; ++b) {
+    const int a = ln_gm_exp(b, 0), bb = ln_gm_exp(b, 1), c = ln_gm_exp(b, 2), e = ln_gm_exp(b, 3);
+    int v = 0;
+    if (which == 0) v = ln_tri(0, ln_plain_slot(c, e), bb);
+    else if (which == 1) v = ln_tri(1, ln_plain_slot(c, e), a);
+    else if (which == 2) v = ln_tri(2, ln_z_u(c + 1, e), bb);
+    else v = 3 - (a + bb + c + e);
+    k |= (unsigned long long)v << (4 * b);
+  }
+  return k;
+}
+constexpr unsigned long long kLnT0 = ln_pack_gm(0), kLnT1 = ln_pack_gm(1), kLnT2 = ln_pack_gm(2),
+                             kLnSlack = ln_pack_gm(3);
+constexpr unsigned long long kLnRB0 = ln_pack_rowbase(0), kLnRB1 = ln_pack_rowbase(1), kLnRB2 = ln_pack_rowbase(2);
+
+// per-warp shared memory of the line kernel (floats), two zones z = 0, 1:
+// w[5][20], g[5][16] (entry 15 of a row unused), the z-projected fluxes (rows
+// at ln_rowbase, 1436 floats; the face stage reuses them) and the second-step
+// outputs [round][vv][tri][m].  The zones' copies of the z-projected fluxes are
+// 16 (mod 32) floats apart and those of the second-step outputs 4 (mod 32):
+// the two zones' lanes then store to disjoint banks in both steps.
+struct LineSmem {
+  static constexpr int W = 0, WS = 100;
+  static constexpr int G = 200, GS = 80;
+  static constexpr int Y2 = 360, Y2S = 1456;
+  static constexpr int Y3 = Y2 + 2 * Y2S - 16, Y3S = 484;   // 3256
+  static constexpr int SIZE = Y3 + 2 * Y3S - 4;              // 4220 per warp
+};
+
+// mass-row sources of the line kernel: as FactIdx::mass_src, with the g rows
+// 16 floats apart
+struct LineIdx {
+  uint8_t mass_src[3][6][16];
+};
+__constant__ LineIdx c_lidx;
+
+// mass row of G-mode b, direction d (line kernel layout): as mass_gmode_dir
+__device__ __forceinline__ float line_mass_dir(const float* zw, const float* zg, const LineIdx& ix, int b, int d,
+                                               float lamd) {
+  const int e = unpack(kGmE, 2, b);
+  const int ow = ix.mass_src[d][0][b], o0 = ix.mass_src[d][1][b], o1 = ix.mass_src[d][2][b];
+  const int o2 = ix.mass_src[d][3][b], o3 = ix.mass_src[d][4][b];
+  const float w = ow != 255 ? zw[ow] : 0.f;
+  const float g0 = o0 != 255 ? zg[o0] : 0.f;
+  const float g1 = o1 != 255 ? zg[o1] : 0.f;
+  const float g2 = o2 != 255 ? zg[o2] : 0.f;
+  const float w3 = o3 != 255 ? zw[o3] : 0.f;
+  const float cw = e == 0 ? 1.f : 0.f;
+  const float c0 = e == 2 ? 0.f : -0.5f;
+  const float c1 = e == 0 ? 1.f / 6.f : e == 2 ? -1.f / 6.f : 0.f;
+  const float c2 = e == 1 ? 0.1f : 0.f;
+  const float m = fmaf(c2, g2, fmaf(c1, g1, fmaf(c0, g0, cw * w)));
+  return lamd * fmaf((float)ix.mass_src[d][5][b], m, 0.1f * w3);
+}
+
+__device__ __forceinline__ float dot4(float4 a, const float* bp) {
+  const float4 b = *reinterpret_cast<const float4*>(bp);
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+// The second and last projection steps and the mass row of the new G (the 16
+// lanes of one zone; y2 holds the z-projected fluxes of the sweep).
+template <int EMAX>
+__device__ __forceinline__ void line_project(const float* y2, float* y3, float* sg, const float* sw,
+                                             const Tabs<float>& tb, const LineIdx& ix, int l16, const float lam[3]) {
+  constexpr int NGE = EMAX == 0 ? 10 : 15;
+  const Tabs<float>& tc = tabs<float>(3);
+  // the mass row reads the previous G: before any lane stores the new one
+  float gmass = 0.f;
+  if (l16 < NGE)
+    gmass = line_mass_dir(sw, sg, ix, l16, 0, lam[0]) + line_mass_dir(sw, sg, ix, l16, 1, lam[1]) +
+            line_mass_dir(sw, sg, ix, l16, 2, lam[2]);
+  const int vv = l16 >> 2, m = l16 & 3;
+  // second step, rounds 0 and 2 contract y (lanes hold i = m), round 1 x (j = m)
 #pragma unroll
-      for (int i1 = 0; i1 < 2; ++i1)
+  for (int R = 0; R < 3; ++R) {
+    const int rb = (int)((R == 0 ? kLnRB0 : R == 1 ? kLnRB1 : kLnRB2) >> (16 * vv)) & 0xffff;
 #pragma unroll
-        for (int p2 = 0; p2 < 4; ++p2) {
-          T acc = T(0);
+    for (int u = 0; u < 6; ++u) {
+      const int s = ln_round_slot(R, u);
+      if (ln_e(s) > EMAX) continue;
+      float y[4];
 #pragma unroll
-          for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[p3idx(p1, p2)], tb.PF[p1][i1], acc);
-          w3[i1][p2] = acc;
+      for (int n = 0; n < 4; ++n) y[n] = y2[rb + s * 16 + (R == 1 ? n + 4 * m : m + 4 * n)];
+#pragma unroll
+      for (int qq = 0; qq <= ln_qmax(R, s); ++qq) {
+        float acc = y[0] * tc.WPN[qq][0];
+#pragma unroll
+        for (int n = 1; n < 4; ++n) acc = fmaf(y[n], tc.WPN[qq][n], acc);
+        y3[((R * 4 + vv) * 10 + ln_tri(R, u, qq)) * 4 + m] = acc;
+      }
+    }
+  }
+  __syncwarp();
+  // last step: G-modes b = m, m + 4, m + 8, m + 12 of variable 1 + vv
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int b = m + 4 * kk;
+    if (b < NGE) {
+      const int a = unpack(kGmA, 2, b), bb = unpack(kGmB, 2, b), c = unpack(kGmC, 2, b);
+      const int slack = unpack(kLnSlack, 4, b);
+      const float4 Y0 = *reinterpret_cast<const float4*>(y3 + ((0 * 4 + vv) * 10 + unpack(kLnT0, 4, b)) * 4);
+      const float4 Y1 = *reinterpret_cast<const float4*>(y3 + ((1 * 4 + vv) * 10 + unpack(kLnT1, 4, b)) * 4);
+      const float4 Yz = *reinterpret_cast<const float4*>(y3 + ((2 * 4 + vv) * 10 + unpack(kLnT2, 4, b)) * 4);
+      const float s0 = dot4(Y0, tb.QN[a][slack]);
+      const float s1 = dot4(Y1, tb.QN[bb][slack]);
+      float s2 = (float)(c + 1) * dot4(Yz, tb.WPN[a]);
+      if (b == 0) {
+        // dP3 = 3 P2 + P0/10: the z-mode 3 coefficient also feeds c = 0
+        const float4 Y3z = *reinterpret_cast<const float4*>(y3 + ((2 * 4 + vv) * 10 + ln_tri(2, 3, 0)) * 4);
+        s2 = fmaf(0.1f, dot4(Y3z, tb.WPN[0]), s2);
+      }
+      sg[(vv + 1) * 16 + b] = fmaf(lam[0], s0, fmaf(lam[1], s1, lam[2] * s2));
+    }
+  }
+  if (l16 < NGE) sg[l16] = gmass;
+  if (EMAX == 0)
+    for (int it = l16; it < 25; it += 16) sg[(it / 5) * 16 + 10 + it % 5] = 0.f;
+  __syncwarp();
+}
+
+// sweep-0 flux rows at one node: Z[r][s] += F_r P_p(z_k) w_k / |P_p|^2 (e = 0)
+// and the time-contracted rows of the later sweeps (all used slots)
+template <int EMAX>
+__device__ __forceinline__ void line_z_accumulate(float (&Z)[9][9], const float (&f)[9][3], int k) {
+  const Tabs<float>& tc = tabs<float>(3);
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+      if (ln_used(r, s) && ln_e(s) <= EMAX) Z[r][s] = fmaf(f[r][ln_e(s)], tc.WPN[ln_p(s)][k], Z[r][s]);
+}
+
+template <int LW>
+__global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, const float* __restrict__ W,
+                                                           const double* __restrict__ d_dt, int picard,
+                                                           float* __restrict__ FS) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kTB = ((sizeof(Tabs<float>) + 15) / 16) * 16;
+  constexpr int kIX = ((sizeof(LineIdx) + 15) / 16) * 16;
+  Tabs<float>& tb = *reinterpret_cast<Tabs<float>*>(smem_raw);
+  LineIdx& ix = *reinterpret_cast<LineIdx*>(smem_raw + kTB);
+  float* smem = reinterpret_cast<float*>(smem_raw + kTB + kIX);
+  {
+    const int* src = reinterpret_cast<const int*>(&tabs<float>(3));
+    int* dst = reinterpret_cast<int*>(&tb);
+    for (int i = threadIdx.x; i < (int)(sizeof(Tabs<float>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    const int8_t* s8 = reinterpret_cast<const int8_t*>(&c_lidx);
+    int8_t* d8 = reinterpret_cast<int8_t*>(&ix);
+    for (int i = threadIdx.x; i < (int)sizeof(LineIdx); i += blockDim.x) d8[i] = s8[i];
+  }
+  __syncthreads();
+  const Tabs<float>& tc = tabs<float>(3);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int zh = lane >> 4, l16 = lane & 15;
+  const int li = l16 & 3, lj = l16 >> 2;   // this lane's line of nodes (x_i, y_j, z_0..3)
+  float* wbase = smem + wib * LineSmem::SIZE;
+  float* sw = wbase + LineSmem::W + zh * LineSmem::WS;
+  float* sg = wbase + LineSmem::G + zh * LineSmem::GS;
+  float* y2 = wbase + LineSmem::Y2 + zh * LineSmem::Y2S;
+  float* y3 = wbase + LineSmem::Y3 + zh * LineSmem::Y3S;
+  const long long nb = box.size();
+  const double dt = *d_dt;
+  float lam[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lam[d] = (float)(dt / q.dx[d]);
+  const float gm1 = (float)(q.gamma - 1.0);
+  // P_a(x_i) P_b(y_j) at this lane's line, a + b <= 3
+  float phi[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4 - a; ++b) phi[a][b] = tb.PN[a][li] * tb.PN[b][lj];
+
+  for (long long r0 = ((long long)blockIdx.x * LW + wib) * 2; r0 < nb; r0 += (long long)gridDim.x * LW * 2) {
+    const long long r = r0 + zh;
+    const bool live = r < nb;   // the last warp may hold one zone only
+    for (int it = l16; it < 100; it += 16) sw[it] = live ? W[(long long)it * nb + r] : (it == 0 || it == 80 ? 1.f : 0.f);
+    for (int it = l16; it < 80; it += 16) sg[it] = 0.f;
+    __syncwarp();
+    // w at the line's four nodes: contract x and y (a + b <= 3 - c), then z
+    float wn[5][4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      float wv[20];
+#pragma unroll
+      for (int k4 = 0; k4 < 5; ++k4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(sw + v * 20 + 4 * k4);
+        wv[4 * k4] = t4.x; wv[4 * k4 + 1] = t4.y; wv[4 * k4 + 2] = t4.z; wv[4 * k4 + 3] = t4.w;
+      }
+      float w2[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b <= 3 - c; ++b)
+#pragma unroll
+          for (int a = 0; a <= 3 - b - c; ++a) acc = fmaf(wv[simplex_idx(3, a, b, c)], phi[a][b], acc);
+        w2[c] = acc;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float acc = w2[0] * tc.PN[0][k];
+#pragma unroll
+        for (int c = 1; c < 4; ++c) acc = fmaf(w2[c], tc.PN[c][k], acc);
+        wn[v][k] = acc;
+      }
+    }
+    if (picard >= 1) {
+      // sweep 0: time-independent flux at the spatial nodes
+      float Z[9][9];
+#pragma unroll
+      for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+        for (int s = 0; s < 9; ++s) Z[rr][s] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float qn[5], f1[9], f[9][3];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qn[v] = wn[v][k];
+        sym_fluxes<float>(qn, 1.f / qn[0], gm1, f1);
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) f[rr][0] = f[rr][1] = f[rr][2] = f1[rr];
+        line_z_accumulate<0>(Z, f, k);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+        for (int s = 0; s < 9; ++s)
+          if (ln_used(rr, s) && ln_e(s) == 0) y2[ln_rowbase(rr) + s * 16 + l16] = Z[rr][s];
+      __syncwarp();
+      line_project<0>(y2, y3, sg, sw, tb, ix, l16, lam);
+    }
+    for (int sweep = 1; sweep < picard; ++sweep) {
+      // C[v][c][t] = sum_{a,b,e} g P_a(x_i) P_b(y_j) I_e(tau_t): the iterate's
+      // correction along the line, z-modes c = 0..2 at the four time nodes
+      float C[5][3][4];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        float gv[16];
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(sg + v * 16 + 4 * k4);
+          gv[4 * k4] = t4.x; gv[4 * k4 + 1] = t4.y; gv[4 * k4 + 2] = t4.z; gv[4 * k4 + 3] = t4.w;
         }
-      // G part per face time point
-      T gv[2][2][2];  // [it][i1][i2]
 #pragma unroll
-      for (int tq = 0; tq < 2; ++tq) {
-        const T* gtv = gt + (v * 2 + tq) * 10;
-        T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index p2idx(p1, p2)
+        for (int c = 0; c < 3; ++c) {
+          float H[3];
 #pragma unroll
-        for (int p2 = 0; p2 <= 2; ++p2)
+          for (int e = 0; e <= 2 - c; ++e) {
+            float acc = 0.f;
 #pragma unroll
-          for (int p1 = 0; p1 <= 2 - p2; ++p1) {
-            T acc = T(0);
+            for (int b = 0; b <= 2 - c - e; ++b)
 #pragma unroll
-            for (int an = 0; an <= 2 - p1 - p2; ++an) {
-              const int m = d == 0 ? tri2idx(an, p1, p2) : d == 1 ? tri2idx(p1, an, p2) : tri2idx(p1, p2, an);
-              acc = fma(gtv[m], tb.PE[an][side], acc);
-            }
-            gn2[p2idx(p1, p2)] = acc;
+              for (int a = 0; a <= 2 - b - c - e; ++a) acc = fmaf(gv[gmidx(a, b, c, e)], phi[a][b], acc);
+            H[e] = acc;
           }
 #pragma unroll
-        for (int i1 = 0; i1 < 2; ++i1) {
-          T g3[3];
+          for (int t = 0; t < 4; ++t) {
+            float acc = H[0] * tc.IT[0][t];
 #pragma unroll
-          for (int p2 = 0; p2 < 3; ++p2) {
-            T acc = T(0);
-#pragma unroll
-            for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[p2idx(p1, p2)], tb.PF[p1][i1], acc);
-            g3[p2] = acc;
-          }
-#pragma unroll
-          for (int i2 = 0; i2 < 2; ++i2) {
-            T acc = T(0);
-#pragma unroll
-            for (int p2 = 0; p2 < 3; ++p2) acc = fma(g3[p2], tb.PF[p2][i2], acc);
-            gv[tq][i1][i2] = acc;
+            for (int e = 1; e <= 2 - c; ++e) acc = fmaf(H[e], tc.IT[e][t], acc);
+            C[v][c][t] = acc;
           }
         }
       }
+      float Z[9][9];
 #pragma unroll
-      for (int i1 = 0; i1 < 2; ++i1)
+      for (int rr = 0; rr < 9; ++rr)
 #pragma unroll
-        for (int i2 = 0; i2 < 2; ++i2) {
-          T acc = T(0);
+        for (int s = 0; s < 9; ++s) Z[rr][s] = 0.f;
 #pragma unroll
-          for (int p2 = 0; p2 < 4; ++p2) acc = fma(w3[i1][p2], tb.PF[p2][i2], acc);
+      for (int k = 0; k < 4; ++k) {
+        NodeAcc<float> acc = {};
 #pragma unroll
-          for (int tq = 0; tq < 2; ++tq) fv[(ds * 8 + i1 + 2 * (i2 + 2 * tq)) * 5 + v] = acc - gv[tq][i1][i2];
+        for (int tp = 0; tp < 2; ++tp) {
+          float f[2][9], qn[2][5];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int t = h ? 3 - tp : tp;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              float x = wn[v][k];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) x = fmaf(-C[v][c][t], tc.PN[c][k], x);
+              qn[h][v] = x;
+            }
+          }
+          float ia, ib;
+          recip_pair<float>(qn[0][0], qn[1][0], ia, ib);
+          sym_fluxes<float>(qn[0], ia, gm1, f[0]);
+          sym_fluxes<float>(qn[1], ib, gm1, f[1]);
+          accumulate_pair<float>(acc, f[0], f[1], tc, tp);
         }
+        line_z_accumulate<2>(Z, acc.a, k);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+        for (int s = 0; s < 9; ++s)
+          if (ln_used(rr, s)) y2[ln_rowbase(rr) + s * 16 + l16] = Z[rr][s];
+      __syncwarp();
+      line_project<2>(y2, y3, sg, sw, tb, ix, l16, lam);
     }
-    __syncwarp();
-    bool bad = false;
-    if (q.fallback)
-      for (int row = lane; row < 48; row += 32) bad = bad || !state_physical5<T>(fv + row * 5, gm1);
-    bad = __any_sync(0xffffffffu, bad) && q.fallback;
-    if (bad && lane == 0 && q.fb_count) atomicAdd(q.fb_count, 1ULL);
-    __syncwarp();
-    for (int it = lane; it < 240; it += 32) {
-      int v = it % 5, row = it / 5;
-      FS[((long long)row * 5 + v) * nb + r] = bad ? sw[v * 20] : fv[row * 5 + v];
+    // face states, one zone after the other, with the whole warp
+#pragma unroll 1
+    for (int zz = 0; zz < 2; ++zz) {
+      const long long rz = r0 + zz;
+      if (rz >= nb) break;
+      fact_face_states<float, 16>(q, wbase + LineSmem::W + zz * LineSmem::WS, wbase + LineSmem::G + zz * LineSmem::GS,
+                                  wbase + LineSmem::Y2 + zz * LineSmem::Y2S, tb, lane, gm1, nb, rz, FS);
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -1012,6 +1430,16 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
     }
   }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_fidx, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
+  // the same sources for the line kernel, whose g rows are 16 floats apart
+  LineIdx hl;
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 6; ++k)
+      for (int b = 0; b < 16; ++b) {
+        uint8_t o = h.mass_src[d][k][b];
+        if (k >= 1 && k <= 3 && o != 255) o = (uint8_t)((o / 15) * 16 + o % 15);
+        hl.mass_src[d][k][b] = o;
+      }
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_lidx, &hl, sizeof(hl), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
 }
@@ -1021,7 +1449,12 @@ template <typename T> static size_t fact_smem(int wpb) {
          (size_t)wpb * FactSmem<T>::SIZE * sizeof(T);
 }
 constexpr int kFactWarpsD = 2;   // FP64: two zones per block, four blocks per SM
-constexpr int kFactWarpsF = 2;   // FP32
+constexpr int kFactWarpsF = 2;   // FP32 (factorised kernel; the line kernel replaces it)
+constexpr int kLineWarps = 2;    // FP32 line kernel: four zones per block
+static size_t line_smem(int lw) {
+  return ((sizeof(Tabs<float>) + 15) / 16) * 16 + ((sizeof(LineIdx) + 15) / 16) * 16 +
+         (size_t)lw * LineSmem::SIZE * sizeof(float);
+}
 
 cudaError_t predict_init(cudaStream_t s) {
   if (g_fact_tables_ready) return cudaSuccess;
@@ -1038,6 +1471,11 @@ cudaError_t predict_init(cudaStream_t s) {
     e = cudaFuncSetAttribute(k_predict_fact<double, kFactWarpsD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_predict_fact<float, kFactWarpsF>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_predict_lines<kLineWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)line_smem(kLineWarps));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_predict_lines<kLineWarps>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) g_fact_tables_ready = true;
   return e;
 }
@@ -1054,10 +1492,11 @@ void launch_predict_tab(const Geo& q, int prec, int picard, const void* W, const
       k_predict_fact<double, kFactWarpsD><<<(int)blocks, 32 * kFactWarpsD, fact_smem<double>(kFactWarpsD), s>>>(
           q, box, (const double*)W, d_dt, picard, (const double*)tab, L, (double*)FS);
     } else {
-      long long blocks = (nb + kFactWarpsF - 1) / kFactWarpsF;
+      const long long zpb = 2 * kLineWarps;   // zones per block
+      long long blocks = (nb + zpb - 1) / zpb;
       if (blocks > 152LL * 256) blocks = 152LL * 256;
-      k_predict_fact<float, kFactWarpsF><<<(int)blocks, 32 * kFactWarpsF, fact_smem<float>(kFactWarpsF), s>>>(
-          q, box, (const float*)W, d_dt, picard, (const float*)tab, L, (float*)FS);
+      k_predict_lines<kLineWarps><<<(int)blocks, 32 * kLineWarps, line_smem(kLineWarps), s>>>(
+          q, box, (const float*)W, d_dt, picard, (float*)FS);
     }
     return;
   }
