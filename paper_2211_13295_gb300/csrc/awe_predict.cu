@@ -1116,6 +1116,8 @@ struct LineIdx {
   uint8_t mass_src[3][6][16];
 };
 __constant__ LineIdx c_lidx;
+// I_e(tau_t) P_c(z_k) for (c, e) = (1, 0), (1, 1), (2, 0): [j][t][k]
+__constant__ float c_ln_itpn[3][4][4];
 
 // mass row of G-mode b, direction d (line kernel layout): as mass_gmode_dir
 __device__ __forceinline__ float line_mass_dir(const float* zw, const float* zg, const LineIdx& ix, int b, int d,
@@ -1255,10 +1257,24 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
 #pragma unroll
     for (int b = 0; b < 4 - a; ++b) phi[a][b] = tb.PN[a][li] * tb.PN[b][lj];
 
-  for (long long r0 = ((long long)blockIdx.x * LW + wib) * 2; r0 < nb; r0 += (long long)gridDim.x * LW * 2) {
-    const long long r = r0 + zh;
-    const bool live = r < nb;   // the last warp may hold one zone only
-    for (int it = l16; it < 100; it += 16) sw[it] = live ? W[(long long)it * nb + r] : (it == 0 || it == 80 ? 1.f : 0.f);
+  // the modes of the next zone pair are loaded while this one is computed
+  // (a zone beyond the box reads a uniform state and stores nothing)
+  const long long rstep = (long long)gridDim.x * LW * 2;
+  float wpre[7];
+  auto fetch = [&](long long rr) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int it = l16 + 16 * k;
+      wpre[k] = it < 100 && rr < nb ? W[(long long)it * nb + rr] : (it == 0 || it == 80 ? 1.f : 0.f);
+    }
+  };
+  long long r0 = ((long long)blockIdx.x * LW + wib) * 2;
+  fetch(r0 + zh);
+  for (; r0 < nb; r0 += rstep) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+      if (l16 + 16 * k < 100) sw[l16 + 16 * k] = wpre[k];
+    fetch(r0 + rstep + zh);
     for (int it = l16; it < 80; it += 16) sg[it] = 0.f;
     __syncwarp();
     // w at the line's four nodes: contract x and y (a + b <= 3 - c), then z
@@ -1315,9 +1331,11 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
       line_project<0>(y2, y3, sg, sw, tb, ix, l16, lam);
     }
     for (int sweep = 1; sweep < picard; ++sweep) {
-      // C[v][c][t] = sum_{a,b,e} g P_a(x_i) P_b(y_j) I_e(tau_t): the iterate's
-      // correction along the line, z-modes c = 0..2 at the four time nodes
-      float C[5][3][4];
+      // The iterate's correction along the line: with H_ce = sum_{a,b} g_abce
+      // P_a(x_i) P_b(y_j), the z-mode 0 part at the four time nodes,
+      // C0[v][t] = sum_e H_0e I_e(tau_t), and the z-mode 1, 2 coefficients H_10,
+      // H_11, H_20, whose products with I_e(tau_t) P_c(z_k) are constants
+      float C0[5][4], H1[5][3];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         float gv[16];
@@ -1326,9 +1344,9 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
           const float4 t4 = *reinterpret_cast<const float4*>(sg + v * 16 + 4 * k4);
           gv[4 * k4] = t4.x; gv[4 * k4 + 1] = t4.y; gv[4 * k4 + 2] = t4.z; gv[4 * k4 + 3] = t4.w;
         }
+        float H[3][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float H[3];
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int e = 0; e <= 2 - c; ++e) {
             float acc = 0.f;
@@ -1336,16 +1354,17 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
             for (int b = 0; b <= 2 - c - e; ++b)
 #pragma unroll
               for (int a = 0; a <= 2 - b - c - e; ++a) acc = fmaf(gv[gmidx(a, b, c, e)], phi[a][b], acc);
-            H[e] = acc;
+            H[c][e] = acc;
           }
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            float acc = H[0] * tc.IT[0][t];
-#pragma unroll
-            for (int e = 1; e <= 2 - c; ++e) acc = fmaf(H[e], tc.IT[e][t], acc);
-            C[v][c][t] = acc;
-          }
+        for (int t = 0; t < 4; ++t) {
+          float acc = H[0][0] * tc.IT[0][t];
+          acc = fmaf(H[0][1], tc.IT[1][t], acc);
+          C0[v][t] = fmaf(H[0][2], tc.IT[2][t], acc);
         }
+        H1[v][0] = H[1][0];
+        H1[v][1] = H[1][1];
+        H1[v][2] = H[2][0];
       }
       float Z[9][9];
 #pragma unroll
@@ -1363,9 +1382,9 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
             const int t = h ? 3 - tp : tp;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              float x = wn[v][k];
+              float x = wn[v][k] - C0[v][t];   // P_0 = 1
 #pragma unroll
-              for (int c = 0; c < 3; ++c) x = fmaf(-C[v][c][t], tc.PN[c][k], x);
+              for (int j = 0; j < 3; ++j) x = fmaf(-H1[v][j], c_ln_itpn[j][t][k], x);
               qn[h][v] = x;
             }
           }
@@ -1440,6 +1459,17 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
         hl.mass_src[d][k][b] = o;
       }
   if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_lidx, &hl, sizeof(hl), 0, cudaMemcpyHostToDevice, s);
+  {
+    Tabs<double> td[3];
+    Tabs<float> tf[3];
+    build_tabs(td, tf);
+    float itpn[3][4][4];
+    const int ce[3][2] = {{1, 0}, {1, 1}, {2, 0}};
+    for (int j = 0; j < 3; ++j)
+      for (int t = 0; t < 4; ++t)
+        for (int k = 0; k < 4; ++k) itpn[j][t][k] = (float)(td[2].IT[ce[j][1]][t] * td[2].PN[ce[j][0]][k]);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ln_itpn, itpn, sizeof(itpn), 0, cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
 }
