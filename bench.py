@@ -301,16 +301,16 @@ def other_configs(world, gate_params):
     forms: the double Mach reflection (4096x1024, order 3, FP32 bulk, with the
     positivity fallback), the Kelvin-Helmholtz layer (512^3, order 4, FP32
     bulk with the trained gate, 64-plane slabs) and the blast (384^3, order 4,
-    FP64 with the trained gate and the positivity fallback, 128-plane slabs).
-    Two timed steps after one warm-up step each; the status after the timed
-    steps is reported (the blast loses positivity in a few zones on its first
-    step, in the oracle as on the GPU)."""
+    FP64 with the trained gate and the a posteriori positivity fallback,
+    128-plane slabs).  Two timed steps after one warm-up step each; the status
+    after the timed steps is reported, and a run that ends non-physical has no
+    rate."""
     import torch
     from paper_2211_13295_gb300 import awe
     from paper_2211_13295_gb300 import problems as P
     runs = [("dmr_4096x1024_o3_fp32_fallback", P.dmr(nx=4096, ny=1024).replace(fallback=True), "fp32", False, 0),
             ("kh3d_512_o4_fp32_gate_slab64", P.kh3d(n=512, order=4), "fp32", True, 64),
-            ("blast3d_384_o4_fp64_gate_fallback_slab128", P.blast3d(n=384, order=4).replace(fallback=True),
+            ("blast3d_384_o4_fp64_gate_fallback2_slab128", P.blast3d(n=384, order=4).replace(fallback=2),
              "fp64", True, 128)]
     out = {}
     for name, prob, prec, gate, slab in runs:
@@ -418,7 +418,8 @@ def gated_forms(args, prob, Uh, U1, zones, world):
         ms = max_over_ranks(ms, world)
         g.close()
         d = {"value": world * zones * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
-             "flagged_fraction": fl / tot, "gate_ms_per_step": prof["gate"][1] / args.steps}
+             "flagged_fraction": fl / tot, "gate_ms_per_step": prof["gate"][1] / args.steps,
+             "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items() if v[0]}}
         if Ug1 is not None:
             sc = np.abs(U1[0]).sum()
             d["rel_l1_vs_full_weno_fp64_one_step"] = max(
@@ -563,6 +564,7 @@ def run_native(args, rank, world, local):
             sci = np.abs(U1[0]).max()
             f32["rel_linf_vs_fp64_gpu_one_step"] = max(
                 float(np.abs(U1f[v] - U1[v]).max() / max(np.abs(U1[v]).max(), sci)) for v in range(5))
+        f32["stage_ms_per_step"] = {k: round(v[1] / args.steps, 3) for k, v in prof32.items() if v[0]}
         forms["fp32_bulk"] = f32
 
     if run_forms:

@@ -118,10 +118,16 @@ typedef struct {
                             (troubled-zone gate); needs awe_gate_set_weights */
   int slab;              /* z zones per slab of the intermediate buffers
                             (3D; 0 = whole domain in one slab) */
-  int fallback;          /* 1: positivity fallback (not in the paper): a zone
+  int fallback;          /* positivity fallback (not in the paper).  1: a zone
                             whose face states have rho <= 0, p <= 0 or a
                             non-finite value uses its zone mean as every face
-                            state (first order) */
+                            state (first order).  2 (ADER, no exchanged faces):
+                            that, and after the update a zone whose new mean is
+                            not physical, with every zone sharing a face with
+                            it, is updated again from the old state with the
+                            Riemann flux between the two old zone means on each
+                            face of a flagged zone (first order, conservative);
+                            4 passes, flags accumulating */
   int riemann;           /* awe_riemann: the corrector's Riemann solver */
   int scheme;            /* awe_scheme: ADER (default) or SSP Runge-Kutta */
   int rk_stages;         /* AWE_SCHEME_SSPRK: 2, 3 or 5 stages (0: 2, 3, 5 at

@@ -211,7 +211,7 @@ class Oracle:
         if prob.pre is not None:
             for v in range(len(prob.pre)):
                 c.pre[v] = prob.pre[v]
-        c.fallback = 1 if getattr(prob, "fallback", False) else 0
+        c.fallback = int(getattr(prob, "fallback", 0) or 0)
         c.riemann = RIEMANN[getattr(prob, "riemann", "hllc")]
         self.cfg = c
         self.dim = prob.dim

@@ -1000,6 +1000,88 @@ double ora_signal_max(const ora_cfg* c, const double* Ug) {
   return smax;
 }
 
+/* A posteriori fallback (not in the paper; fallback = 2).  After the update,
+ * a zone whose new mean is not physical is flagged; every flagged zone and
+ * every zone sharing a face with one is updated again from the old state,
+ * with the flux of each face next to a flagged zone replaced by the Riemann
+ * flux between the two old zone means (first order), the high-order flux on
+ * every other face.  Both zones of a face use the same flux, so the update
+ * stays conservative; a fully first-order zone stays physical under the
+ * positivity condition of the first-order scheme (its CFL sum below 1/2).
+ * Flags accumulate over ORA_FB_PASSES passes (a zone that a first-order
+ * neighbour makes non-physical is flagged in the next pass).  Across a
+ * periodic face the neighbour is the periodic image; other boundary faces
+ * have no neighbour to flag. */
+#define ORA_FB_PASSES 4
+static int fb_neighbour(const geom* q, int idx[3], int d, int s, const ora_cfg* c, size_t* out) {
+  int m[3] = {idx[0], idx[1], idx[2]};
+  m[d] += s;
+  if (m[d] < 0 || m[d] >= q->n[d]) {
+    if (c->bc[2 * d + (s > 0)] != 0) return 0; /* not periodic: no neighbour */
+    m[d] = (m[d] + q->n[d]) % q->n[d];
+  }
+  *out = ((size_t)m[2] * q->n[1] + m[1]) * q->n[0] + m[0];
+  return 1;
+}
+
+static void a_posteriori_fallback(const ora_cfg* c, const geom* q, const double* Ug, double dt, const double* F,
+                                  const size_t* offs, const size_t* nfs, double* Uout) {
+  const int dim = q->dim, nv = q->nv;
+  const size_t nact = (size_t)q->n[0] * q->n[1] * q->n[2];
+  unsigned char* fl = (unsigned char*)calloc(nact, 1);
+  double* Unew = (double*)malloc(sizeof(double) * nv * nact);
+  for (int pass = 0; pass < ORA_FB_PASSES; ++pass) {
+    for (size_t z = 0; z < nact; ++z) {
+      double U[MAXV];
+      for (int v = 0; v < nv; ++v) U[v] = Uout[(size_t)v * nact + z];
+      if (!zone_physical(q, c->gamma, U)) fl[z] = 1;
+    }
+    memcpy(Unew, Uout, sizeof(double) * nv * nact);
+    for (size_t z = 0; z < nact; ++z) {
+      int idx[3] = {(int)(z % q->n[0]), (int)((z / q->n[0]) % q->n[1]), (int)(z / ((size_t)q->n[0] * q->n[1]))};
+      /* flags of the zone and of its neighbours below (s = -1) and above (s = +1) in each direction */
+      int near = fl[z], nfl[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+      for (int d = 0; d < dim; ++d)
+        for (int si = 0; si < 2; ++si) {
+          size_t w;
+          if (fb_neighbour(q, idx, d, si ? 1 : -1, c, &w) && fl[w]) {
+            nfl[d][si] = 1;
+            near = 1;
+          }
+        }
+      if (!near) continue;
+      int gi = idx[0] + q->g, gj = dim >= 2 ? idx[1] + q->g : idx[1], gk = dim == 3 ? idx[2] + q->g : 0;
+      double U0[MAXV];
+      for (int v = 0; v < nv; ++v) U0[v] = Ug[v * q->ntot + gidx(q, gi, gj, gk)];
+      double acc[MAXV] = {0, 0, 0, 0, 0};
+      for (int d = 0; d < dim; ++d) {
+        int E[3] = {q->n[0], q->n[1], q->n[2]};
+        E[d] += 1;
+        double Ffo[2][MAXV];  /* faces below (0) and above (1) */
+        for (int si = 0; si < 2; ++si) {
+          int fi[3] = {idx[0], idx[1], idx[2]};
+          fi[d] += si;
+          size_t f = ((size_t)fi[2] * E[1] + fi[1]) * E[0] + fi[0];
+          if (fl[z] || nfl[d][si]) {
+            int m[3] = {gi, gj, gk};
+            m[d] += si ? 1 : -1;
+            double Un[MAXV], *UL = si ? U0 : Un, *UR = si ? Un : U0;
+            for (int v = 0; v < nv; ++v) Un[v] = Ug[v * q->ntot + gidx(q, m[0], m[1], m[2])];
+            ora_riemann(c->riemann, dim, c->gamma, d, UL, UR, Ffo[si]);
+          } else {
+            for (int v = 0; v < nv; ++v) Ffo[si][v] = F[offs[d] + (size_t)v * nfs[d] + f];
+          }
+        }
+        for (int v = 0; v < nv; ++v) acc[v] += (dt / q->dx[d]) * (Ffo[1][v] - Ffo[0][v]);
+      }
+      for (int v = 0; v < nv; ++v) Unew[(size_t)v * nact + z] = U0[v] - acc[v];
+    }
+    memcpy(Uout, Unew, sizeof(double) * nv * nact);
+  }
+  free(Unew);
+  free(fl);
+}
+
 /* One step (Make_dU_dt and Update_U_Timestep, Figs. 6-7):
  * U+ = U - dt * sum_d (F_{d,i+1/2} - F_{d,i-1/2}) / dx_d on the active zones. */
 int ora_step(const ora_cfg* c, const double* Ug, double dt, const unsigned char* flags, double* Uout,
@@ -1042,6 +1124,18 @@ int ora_step(const ora_cfg* c, const double* Ug, double dt, const unsigned char*
     if (!zone_physical(&q, c->gamma, U)) bad = 1;
     double s = zone_signal(&q, c->gamma, U);
     if (s > sm) sm = s;
+  }
+  if (c->fallback == 2) {
+    a_posteriori_fallback(c, &q, Ug, dt, F, offs, nfs, Uout);
+    bad = 0;
+    sm = 0.0;
+    for (size_t z = 0; z < nact; ++z) {
+      double U[MAXV];
+      for (int v = 0; v < nv; ++v) U[v] = Uout[(size_t)v * nact + z];
+      if (!zone_physical(&q, c->gamma, U)) bad = 1;
+      double s = zone_signal(&q, c->gamma, U);
+      if (s > sm) sm = s;
+    }
   }
   free(F);
   if (smax) *smax = sm;

@@ -43,7 +43,9 @@ typedef struct {
   int bc[6];            /* xlo, xhi, ylo, yhi, zlo, zhi */
   double inflow[6][5];  /* fixed conserved state per face (inflow / DMR post-shock) */
   double pre[5];        /* DMR pre-shock conserved state (top boundary) */
-  int fallback;         /* 1: positivity fallback of the face states (see ora.c) */
+  int fallback;         /* 1: positivity fallback of the face states; 2: that and the
+                           a posteriori first-order update of non-physical zones
+                           (see ora.c) */
   int riemann;          /* ORA_RS_*: Riemann solver of the corrector (HLLC by default) */
 } ora_cfg;
 

@@ -170,7 +170,7 @@ def make_config(prob, prec="fp64", gate=False, slab=0, cfl=None, picard=None) ->
     c.cfl = prob.cfl if cfl is None else cfl
     c.gate = 1 if gate else 0
     c.slab = slab
-    c.fallback = 1 if getattr(prob, "fallback", False) else 0
+    c.fallback = int(getattr(prob, "fallback", 0) or 0)
     c.riemann = RIEMANN[getattr(prob, "riemann", "hllc")]
     c.scheme = SCHEME[getattr(prob, "scheme", "ader")]
     c.rk_stages = int(getattr(prob, "rk_stages", 0))

@@ -67,6 +67,12 @@ struct awe_grid {
   double* Urk[2] = {nullptr, nullptr};  // Runge-Kutta stage states (ghosted)
   awe::RKScheme rk;
   int next_stage = 0;       // stage of the current step that runs next (awe_stage)
+  // a posteriori fallback (cfg.fallback = 2): whole-grid high-order fluxes,
+  // zone flags, and scratch targets of the first update's CFL max and status
+  double* Ffb = nullptr;
+  unsigned char* fbflag = nullptr;
+  unsigned long long* d_smax2 = nullptr;
+  int* d_err2 = nullptr;
   double* halo_stage = nullptr;  // host-pointer halo transfers [halo_count]
   bool poison = false;  // AWE_POISON=1 at create: NaN-fill the intermediates before use
   long long szX = 0, szY = 0, szXY = 0, szW = 0, szFS = 0, szF = 0;
@@ -255,10 +261,22 @@ void run_slab(awe_grid* g, int z0, int z1, bool do_flux, bool do_update, const u
   int m3 = prof_mark(g);
   prof_span(g, K_FLUX, m2, m3);
   if (!do_update) return;
-  launch_update(q, g->prec, g->U[g->cur], g->F, g->d_scal + 1, z0, z1, g->U[1 - g->cur], g->d_smax,
-                g->d_err, g->s);
+  const bool post = g->cfg.fallback == 2;
+  launch_update(q, g->prec, g->U[g->cur], g->F, g->d_scal + 1, z0, z1, g->U[1 - g->cur],
+                post ? g->d_smax2 : g->d_smax, post ? g->d_err2 : g->d_err, g->s);
+  if (post) launch_store_fluxes(q, g->prec, g->F, z0, z1, g->Ffb, g->s);
   int m4 = prof_mark(g);
   prof_span(g, K_UPD, m3, m4);
+}
+
+// a posteriori fallback after the whole update, then the CFL max and the
+// status of the final state
+void fallback_passes(awe_grid* g) {
+  int a = prof_mark(g);
+  launch_fb_passes(g->q, g->U[g->cur], g->U[1 - g->cur], g->Ffb, g->fbflag, g->d_scal + 1, kFallbackPasses, g->s);
+  launch_signal_max(g->q, g->U[1 - g->cur], g->d_smax, g->d_err, g->s);
+  int b = prof_mark(g);
+  prof_span(g, K_MISC, a, b);
 }
 
 void fill_ghosts(awe_grid* g, double* U = nullptr, double c = 0.0) {
@@ -433,6 +451,7 @@ int run_stage(awe_grid* g, int k, double dt) {
       slab_range(g, sidx, z0, z1);
       run_slab(g, z0, z1, true, true, flags);
     }
+    if (g->cfg.fallback == 2) fallback_passes(g);
   }
   g->next_stage = k + 1;
   if (k == stage_count(g) - 1) {
@@ -475,7 +494,13 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
     // exchanged face would reconstruct its zones with different weights
     if (c.bc[f] == AWE_BC_EXCHANGE && c.gate)
       return fail(nullptr, AWE_ERR_ARG, "the gate cannot be combined with AWE_BC_EXCHANGE");
+    // the a posteriori fallback's flags would have to cross exchanged faces
+    if (c.bc[f] == AWE_BC_EXCHANGE && c.fallback == 2)
+      return fail(nullptr, AWE_ERR_ARG, "fallback 2 cannot be combined with AWE_BC_EXCHANGE");
   }
+  if (c.fallback < 0 || c.fallback > 2) return fail(nullptr, AWE_ERR_ARG, "fallback must be 0, 1 or 2");
+  if (c.fallback == 2 && c.scheme != AWE_SCHEME_ADER)
+    return fail(nullptr, AWE_ERR_ARG, "fallback 2 (a posteriori) is defined for the ADER scheme");
   if (!(c.gamma > 1.0)) return fail(nullptr, AWE_ERR_ARG, "gamma must exceed 1");
   if (c.picard < 0 || c.picard > 8) return fail(nullptr, AWE_ERR_ARG, "picard out of range");
   if (c.slab < 0) return fail(nullptr, AWE_ERR_ARG, "negative slab");
@@ -595,6 +620,15 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
     allocs.push_back({(void**)&g->Urk[0], nbytesU, "Runge-Kutta stage state"});
     allocs.push_back({(void**)&g->Urk[1], nbytesU, "Runge-Kutta stage state"});
   }
+  if (c.fallback == 2) {
+    long long nff = 0;
+    for (int d = 0; d < q.dim; ++d)
+      nff += (long long)(q.n[0] + (d == 0)) * (q.n[1] + (d == 1)) * (q.dim == 3 ? q.n[2] + (d == 2) : 1) * q.nv;
+    allocs.push_back({(void**)&g->Ffb, sizeof(double) * nff, "whole-grid fluxes (fallback 2)"});
+    allocs.push_back({(void**)&g->fbflag, (size_t)nactive(q), "fallback flags"});
+    allocs.push_back({(void**)&g->d_smax2, sizeof(unsigned long long), "smax scratch"});
+    allocs.push_back({(void**)&g->d_err2, sizeof(int), "status scratch"});
+  }
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) {
@@ -648,7 +682,7 @@ int awe_destroy(awe_grid* g) {
   cudaStreamSynchronize(g->s);
   void* ptrs[] = {g->U[0], g->U[1], g->d_scal, g->d_smax,  g->d_err,  g->X,    g->Y,
                   g->XY,   g->W,    g->FS,     g->F,      g->stage,  g->ptab, g->Urk[0],
-                  g->Urk[1], g->d_fb, g->halo_stage};
+                  g->Urk[1], g->d_fb, g->halo_stage, g->Ffb, g->fbflag, g->d_smax2, g->d_err2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   awe::gate_free(g->gate);

@@ -506,6 +506,11 @@ void launch_fill_ghosts(const Geo& q, double* U, const double* d_t, const double
                         cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 long long halo_count(const Geo& q);
+// a posteriori fallback (awe_flux.cu)
+void launch_store_fluxes(const Geo& q, int prec, const void* F, int z0, int z1, double* Ffull, cudaStream_t s);
+void launch_fb_passes(const Geo& q, const double* Uold, double* Unew, const double* Ffull, unsigned char* flags,
+                      const double* d_dt, int passes, cudaStream_t s);
+constexpr int kFallbackPasses = 4;
 void launch_halo(const Geo& q, double* U, int side, double* buf, bool pack, cudaStream_t s);
 void launch_signal_max(const Geo& q, const double* U, unsigned long long* smax, int* err,
                        cudaStream_t s);

@@ -51,7 +51,7 @@ class Problem:
     lin: tuple = ()
     picard: int = 0
     seed: Optional[int] = None
-    fallback: bool = False               # opt-in positivity fallback of the face states
+    fallback: int = 0                    # opt-in positivity fallback: 1 face states, 2 also a posteriori
     riemann: str = "hllc"                # corrector's Riemann solver: hllc, hll, hllem, rusanov
     scheme: str = "ader"                 # time stepping: ader, or ssprk (Table IV's comparison)
     rk_stages: int = 0                   # SSP-RK stages (2, 3, 5); 0: 2, 3, 5 at orders 2, 3, 4

@@ -46,8 +46,11 @@ def cut(Ug, prob, c, m, g, extra=0):
 def window_problem(prob, m, extra=0):
     n = tuple((m + 2 * extra) if d < prob.dim else 1 for d in range(3))
     hi = tuple(prob.dx(d) * n[d] if d < prob.dim else 1.0 for d in range(3))
+    # outflow: no periodic image across the window's edge (the a posteriori
+    # fallback looks for flagged neighbours there); the ghosts come from the
+    # full array
     return P.Problem("uniform", prob.dim, n, (0, 0, 0), hi, prob.order, gamma=prob.gamma,
-                     fallback=prob.fallback)
+                     fallback=prob.fallback, bc=("outflow",) * 6)
 
 
 def sampled_windows(prob, U0, U1, dt, t, nwin, m, seed, flags_params=None, centers=None):
@@ -188,34 +191,84 @@ def nonphysical_zones(U, gamma):
         return np.argwhere(~((rho > 0) & (p > 0) & np.isfinite(p)))
 
 
-def test_blast_384_order4_gate_fallback_slabbed(awe):
-    """Blast on 384^3, order 4, FP64 with the positivity fallback,
-    slab-streamed (128 planes), first with full WENO, then with a gate that
-    flags large stencil jumps (the oracle computes its own flags).
+def central_windows(prob, U0, U1, dt, centers, m, inner, flags_params=None):
+    """oracle windows of m^3 active zones around each centre; only the central
+    inner^3 zones are compared (the a posteriori fallback of a zone depends on
+    the flags of zones up to a few faces away, which the window's edge does
+    not see)"""
+    g = prob.order
+    N = g - 1
+    Ug = ghosted_full(prob, U0, 0.0)
+    errs = []
+    for c0 in centers:
+        c = [min(max(int(c0[d]) - m // 2, 0), prob.n[d] - m) for d in range(3)]
+        win = np.ascontiguousarray(cut(Ug, prob, c, m, g))
+        flags = None
+        if flags_params is not None:
+            ex = N + 1
+            big = np.ascontiguousarray(cut(Ug, prob, c, m, g, extra=ex))
+            bo = oracle.Oracle(window_problem(prob, m, extra=ex))
+            fb = bo.gate_flags_ghosted(big, flags_params)
+            inr = tuple(slice(ex, ex + m + 2 * g) for _ in range(3))
+            flags = np.ascontiguousarray(fb[inr])
+        Uo, _, rc = oracle.Oracle(window_problem(prob, m)).step_ghosted(win, dt, flags)
+        o = (m - inner) // 2
+        sl = [slice(c[d] + o, c[d] + o + inner) for d in range(3)]
+        Ugpu = U1[:, sl[2], sl[1], sl[0]]
+        errs.append(window_err(Ugpu, Uo[:, o:o + inner, o:o + inner, o:o + inner]))
+    return errs
 
-    At this size the first step leaves a few zones just outside the sphere's
-    surface with negative pressure, in the oracle as on the GPU: the fallback
-    keeps the face states and hence the Riemann problems physical, not the
-    updated means.  The test therefore checks (a) that the GPU reports the
-    non-physical status exactly when its state holds such zones, (b) windows
-    around those zones against the oracle (same values, so the oracle finds
-    the same zones non-physical), and (c) windows on the sphere's surface."""
-    prob = P.blast3d(n=384, order=4).replace(fallback=True)
-    nin, _ = awe.gate_dims(3, 4)
-    U0 = prob.initial_state()
+
+def test_blast_384_order4_gate_fallback_slabbed(awe):
+    """C4, the blast on 384^3, order 4, FP64, slab-streamed (128 planes), with
+    full WENO and with a gate that flags large stencil jumps (the oracle
+    computes its own flags).  With the face-state fallback alone the first
+    step leaves a few zones just outside the sphere with negative pressure;
+    with the a posteriori fallback (fallback 2) it is physical everywhere, and
+    windows centred on those zones, and on the sphere's surface, match the
+    oracle's fallback-2 step."""
     n = 384
+    prob1 = P.blast3d(n=n, order=4).replace(fallback=1)
+    prob2 = prob1.replace(fallback=2)
+    nin, _ = awe.gate_dims(3, 4)
+    U0 = prob1.initial_state()
     r0 = int(0.5 * n + 0.2 * n) - 2
-    surface = [[r0, n // 2, n // 2], [n // 2, r0, n // 2 - 3], [n // 2 - 2, n // 2, r0], [100, 120, 140]]
+    surface = [[r0, n // 2, n // 2], [n // 2, r0, n // 2 - 3], [n // 2 - 2, n // 2, r0]]
     params = jump_gate(nin, 3)
     for gate in (None, params):
-        U1, dt, code = run_one_status(awe, prob, U0, gate=gate, slab=128)
-        bad = nonphysical_zones(U1, prob.gamma)
-        assert code == (awe.AWE_ERR_NONPHYSICAL if len(bad) else awe.AWE_OK), (code, len(bad))
-        centers = [[min(max(int(i) - 1, 0), n - 4), min(max(int(j) - 1, 0), n - 4), min(max(int(k) - 1, 0), n - 4)]
-                   for (k, j, i) in bad[:3]] + surface
-        errs = sampled_windows(prob, U0, U1, dt, 0.0, nwin=len(centers), m=4, seed=3,
-                               flags_params=gate, centers=centers)
+        U1, dt, code1 = run_one_status(awe, prob1, U0, gate=gate, slab=128)
+        bad = nonphysical_zones(U1, prob1.gamma)
+        assert code1 == (awe.AWE_ERR_NONPHYSICAL if len(bad) else awe.AWE_OK), (code1, len(bad))
+        U2, dt2, code2 = run_one_status(awe, prob2, U0, gate=gate, slab=128)
+        assert dt2 == dt and code2 == awe.AWE_OK and len(nonphysical_zones(U2, prob2.gamma)) == 0
+        centers = [[int(i), int(j), int(k)] for (k, j, i) in bad[:3]] + surface
+        errs = central_windows(prob2, U0, U2, dt, centers, m=12, inner=4, flags_params=gate)
         assert max(errs) <= 1e-12, (gate is not None, errs)
+
+
+def test_blast_384_twenty_steps_stay_physical_and_conservative(awe):
+    """C4 over 20 steps (FP64, the jump gate, the a posteriori fallback,
+    128-plane slabs): status OK after every step, and the totals of mass,
+    momentum and energy kept to round-off (the blast wave stays far inside
+    the domain, whose boundary is uniform ambient gas at rest: zero mass and
+    energy flux, opposite pressure forces)."""
+    n = 384
+    prob = P.blast3d(n=n, order=4).replace(fallback=2)
+    nin, _ = awe.gate_dims(3, 4)
+    U0 = prob.initial_state()
+    g = awe.Grid(prob, gate=True, slab=128)
+    g.gate_set_weights(jump_gate(nin, 3))
+    g.set_state(U0)
+    g.cfl_dt()
+    for _ in range(20):
+        g.step(0.0, sync=False)
+        g.check()
+    U = g.get_state()
+    g.close()
+    assert len(nonphysical_zones(U, prob.gamma)) == 0
+    for v in range(5):
+        scale = np.abs(U0[v]).sum() if v in (0, 4) else np.abs(U0[0]).sum()
+        assert abs(U[v].sum() - U0[v].sum()) <= 1e-12 * scale, v
 
 
 def test_kh_512_order4_fp32_gate_slabbed(awe):
