@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(128) k_recon_z(Geo q, Region rx, Region ry, Re
     auto Wp = [&](int v, int a, int b_, int c) -> T& {
       return W[((long long)v * NS + mode_index<D, N>(a, b_, c)) * nb + r];
     };
-#pragma unroll
+    // one variable at a time: unrolled over the five, the pass held every
+    // variable's stencils at once (255 registers and spills at order 4)
+#pragma unroll 1
     for (int v = 0; v < D + 2; ++v) {
       // (0,0,c) from the means
       const double* u = U + v * q.ntot + c0;
