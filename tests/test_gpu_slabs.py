@@ -125,3 +125,29 @@ def test_halo_buffers_by_hand(awe):
     assert np.array_equal(lo, ext[:, :gw])
     assert np.array_equal(hi, ext[:, -gw:])
     g.close()
+
+
+@pytest.mark.parametrize("bc,scheme", [("periodic", "ader"), ("outflow", "ader"), ("periodic", "ssprk")])
+def test_distributed_slab_grid_on_one_rank(awe, bc, scheme):
+    """slabs.DistSlabGrid with a single rank: the path the multi-GPU bench runs
+    (device halo buffers, the exchange object -- a periodic self-exchange here
+    -- the stage loop, the device-resident dt through get_dt/set_dt) must step
+    exactly like the plain grid."""
+    from paper_2211_13295_gb300 import slabs
+    prob, U = make(3, 4, (7, 6, 9), "shock", bc=bc)
+    prob = prob.replace(scheme=scheme)
+    g = awe.Grid(prob)
+    g.set_state(U)
+    g.cfl_dt()
+    d = slabs.DistSlabGrid(prob, 0, 1)
+    d.set_state(d.local(U))
+    d.cfl_dt()
+    for _ in range(3):
+        g.step(0.0, sync=False)
+        d.step(0.0)
+    g.check()
+    d.check()
+    assert np.array_equal(g.get_state(), d.get_state())
+    assert g.get_dt() == d.sub.get_dt()
+    g.close()
+    d.close()
