@@ -262,15 +262,31 @@ class Grid:
         _check(lib().awe_halo_size(self.h, C.byref(n)), self.h)
         return n.value
 
+    def _buffer(self, buf, count, what):
+        """pointer of a float64 buffer of at least `count` elements: a
+        contiguous numpy array, or a contiguous tensor on the host or on the
+        grid's device (the C entry points cannot see a buffer's extent)"""
+        if isinstance(buf, np.ndarray):
+            if buf.dtype != np.float64 or not buf.flags["C_CONTIGUOUS"] or buf.size < count:
+                raise ValueError(f"{what}: need a contiguous float64 array of {count} elements")
+        else:
+            import torch
+            if not isinstance(buf, torch.Tensor) or buf.dtype != torch.float64 or not buf.is_contiguous() \
+                    or buf.numel() < count:
+                raise ValueError(f"{what}: need a contiguous float64 tensor of {count} elements")
+            if buf.is_cuda and buf.device.index != torch.cuda.current_device():
+                raise ValueError(f"{what}: the tensor is not on the current device")
+        return _ptr(buf)
+
     def halo_pack(self, side, out):
         """planes next to face `side` of the next stage's input into `out`
         (numpy array or contiguous float64 tensor of halo_size() elements)"""
-        p, dev = _ptr(out)
+        p, dev = self._buffer(out, self.halo_size(), "halo_pack")
         _check(lib().awe_halo_pack(self.h, int(side), p, dev), self.h)
         return out
 
     def halo_unpack(self, side, buf):
-        p, dev = _ptr(buf)
+        p, dev = self._buffer(buf, self.halo_size(), "halo_unpack")
         _check(lib().awe_halo_unpack(self.h, int(side), p, dev), self.h)
 
     def get_dt(self, out=None):
@@ -280,7 +296,7 @@ class Grid:
             v = C.c_double()
             _check(lib().awe_get_dt(self.h, C.byref(v), 0), self.h)
             return v.value
-        p, dev = _ptr(out)
+        p, dev = self._buffer(out, 1, "get_dt")
         _check(lib().awe_get_dt(self.h, p, dev), self.h)
         return out
 
@@ -290,7 +306,7 @@ class Grid:
             v = C.c_double(float(dt))
             _check(lib().awe_set_dt(self.h, C.byref(v), 0), self.h)
         else:
-            p, dev = _ptr(dt)
+            p, dev = self._buffer(dt, 1, "set_dt")
             _check(lib().awe_set_dt(self.h, p, dev), self.h)
 
     def fallback_count(self):

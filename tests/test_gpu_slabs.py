@@ -103,6 +103,11 @@ def test_subdomain_contract(awe):
     with pytest.raises(awe.AweError) as e:
         g.stage(1, 1e-3)
     assert e.value.code == awe.AWE_ERR_STATE
+    # the binding refuses buffers the C entry points would overrun
+    with pytest.raises(ValueError):
+        g.halo_pack(0, np.zeros(g.halo_size() - 1))
+    with pytest.raises(ValueError):
+        g.halo_unpack(1, np.zeros(g.halo_size(), dtype=np.float32))
     g.close()
 
 
