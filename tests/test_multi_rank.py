@@ -1,9 +1,9 @@
 """The N > 1 host path of bench.py on CPU ranks (gloo, world size 2): the
 timing reduction (max over ranks), the barrier, and the reference arm under
 torchrun (rank 0 alone runs and prints one JSON line, the other rank exits 0
-without work).  The native arm runs N independent replicas (the path is
-sharded by whole problems, no data-path collective), so its only
-cross-rank operations are these."""
+without work).  The native arm's data-path exchange (one z-slab per rank,
+halo planes and the MIN of dt) is slabs.DistSlabGrid, whose host logic is
+tested on gloo ranks in test_slabs_gloo.py."""
 import json
 import os
 import socket
