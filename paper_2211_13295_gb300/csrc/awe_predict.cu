@@ -593,6 +593,103 @@ __device__ __forceinline__ void store_node_y1(T* Y1, int s, const NodeAcc<T>& ac
 // the normal axis at +-1/2 and the two transverse axes at the face Gauss
 // points, the positivity fallback and the store.  sg holds G with rows GS
 // entries apart; scratch takes 340 entries.
+// Time integral of G at the two face time points (shared by all directions
+// of a zone): gt[v][it][tri], 100 entries, over `nl` lanes from lane l0.
+template <typename T, int GS>
+__device__ __forceinline__ void face_gt(const T* sg, T* gt, const Tabs<T>& tb, int l0, int nl) {
+  for (int it = l0; it < 100; it += nl) {
+    int tr = it % 10, rest = it / 10, tq = rest % 2, v = rest / 2;
+    const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
+    T acc = T(0);
+    for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * GS + gm_fast(a, b, c, e)], tb.ITF[e][tq], acc);
+    gt[it] = acc;
+  }
+}
+
+// Face values of one (variable v, direction-side ds) combination: the normal
+// axis at +-1/2, then the two transverse axes at the face Gauss points, for the
+// w part and, per face time point, the G part.  fv[(ds*8 + q)*5 + v], q = i1 +
+// 2*(i2 + 2*it), as the probes document.
+template <typename T>
+__device__ __forceinline__ void face_values_one(const T* sw, const T* gt, T* fv, const Tabs<T>& tb, int v, int ds) {
+  const int d = ds >> 1, side = ds & 1;
+  // axes: n = d (normal), t1 < t2 the transverse ones.  Every loop below
+  // is unrolled over compile-time exponents; the mode index of (an on the
+  // normal axis, p1 on t1, p2 on t2) is one of three constants, picked by d
+  // w part: contract the normal axis at the face, then t1, then t2
+  T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index p3idx(p1, p2)
+#pragma unroll
+  for (int p2 = 0; p2 <= 3; ++p2)
+#pragma unroll
+    for (int p1 = 0; p1 <= 3 - p2; ++p1) {
+      T acc = T(0);
+#pragma unroll
+      for (int an = 0; an <= 3 - p1 - p2; ++an) {
+        const int m = d == 0 ? simplex_idx(3, an, p1, p2) : d == 1 ? simplex_idx(3, p1, an, p2)
+                                                                  : simplex_idx(3, p1, p2, an);
+        acc = fma(sw[v * 20 + m], tb.PE[an][side], acc);
+      }
+      wn2[p3idx(p1, p2)] = acc;
+    }
+  T w3[2][4];  // [i1][p2]
+#pragma unroll
+  for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+    for (int p2 = 0; p2 < 4; ++p2) {
+      T acc = T(0);
+#pragma unroll
+      for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[p3idx(p1, p2)], tb.PF[p1][i1], acc);
+      w3[i1][p2] = acc;
+    }
+  // G part per face time point
+  T gv[2][2][2];  // [it][i1][i2]
+#pragma unroll
+  for (int tq = 0; tq < 2; ++tq) {
+    const T* gtv = gt + (v * 2 + tq) * 10;
+    T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index p2idx(p1, p2)
+#pragma unroll
+    for (int p2 = 0; p2 <= 2; ++p2)
+#pragma unroll
+      for (int p1 = 0; p1 <= 2 - p2; ++p1) {
+        T acc = T(0);
+#pragma unroll
+        for (int an = 0; an <= 2 - p1 - p2; ++an) {
+          const int m = d == 0 ? tri2idx(an, p1, p2) : d == 1 ? tri2idx(p1, an, p2) : tri2idx(p1, p2, an);
+          acc = fma(gtv[m], tb.PE[an][side], acc);
+        }
+        gn2[p2idx(p1, p2)] = acc;
+      }
+#pragma unroll
+    for (int i1 = 0; i1 < 2; ++i1) {
+      T g3[3];
+#pragma unroll
+      for (int p2 = 0; p2 < 3; ++p2) {
+        T acc = T(0);
+#pragma unroll
+        for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[p2idx(p1, p2)], tb.PF[p1][i1], acc);
+        g3[p2] = acc;
+      }
+#pragma unroll
+      for (int i2 = 0; i2 < 2; ++i2) {
+        T acc = T(0);
+#pragma unroll
+        for (int p2 = 0; p2 < 3; ++p2) acc = fma(g3[p2], tb.PF[p2][i2], acc);
+        gv[tq][i1][i2] = acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+    for (int i2 = 0; i2 < 2; ++i2) {
+      T acc = T(0);
+#pragma unroll
+      for (int p2 = 0; p2 < 4; ++p2) acc = fma(w3[i1][p2], tb.PF[p2][i2], acc);
+#pragma unroll
+      for (int tq = 0; tq < 2; ++tq) fv[(ds * 8 + i1 + 2 * (i2 + 2 * tq)) * 5 + v] = acc - gv[tq][i1][i2];
+    }
+}
+
 template <typename T, int GS>
 __device__ __forceinline__ void fact_face_states(const Geo& q, const T* sw, const T* sg, T* scratch,
                                                  const Tabs<T>& tb, int lane, T gm1, long long nb, long long r,
@@ -604,92 +701,9 @@ __device__ __forceinline__ void fact_face_states(const Geo& q, const T* sw, cons
   // q = i1 + 2*(i2 + 2*it), as the probes document.
   T* fv = scratch;                      // [48][5] face values
   T* gt = fv + 240;                     // [v][it][tri] time-integrated G, 100
-  for (int it = lane; it < 100; it += 32) {
-    int tr = it % 10, rest = it / 10, tq = rest % 2, v = rest / 2;
-    const int a = unpack(kTri2P, 2, tr), b = unpack(kTri2Q, 2, tr), c = unpack(kTri2R, 2, tr);
-    T acc = T(0);
-    for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(sg[v * GS + gm_fast(a, b, c, e)], tb.ITF[e][tq], acc);
-    gt[it] = acc;
-  }
+  face_gt<T, GS>(sg, gt, tb, lane, 32);
   __syncwarp();
-  if (lane < 30) {
-    const int v = lane % 5, ds = lane / 5, d = ds >> 1, side = ds & 1;
-    // axes: n = d (normal), t1 < t2 the transverse ones.  Every loop below
-    // is unrolled over compile-time exponents; the mode index of (an on the
-    // normal axis, p1 on t1, p2 on t2) is one of three constants, picked by d
-    // w part: contract the normal axis at the face, then t1, then t2
-    T wn2[10];  // (p1, p2) with p1 + p2 <= 3, index p3idx(p1, p2)
-#pragma unroll
-    for (int p2 = 0; p2 <= 3; ++p2)
-#pragma unroll
-      for (int p1 = 0; p1 <= 3 - p2; ++p1) {
-        T acc = T(0);
-#pragma unroll
-        for (int an = 0; an <= 3 - p1 - p2; ++an) {
-          const int m = d == 0 ? simplex_idx(3, an, p1, p2) : d == 1 ? simplex_idx(3, p1, an, p2)
-                                                                    : simplex_idx(3, p1, p2, an);
-          acc = fma(sw[v * 20 + m], tb.PE[an][side], acc);
-        }
-        wn2[p3idx(p1, p2)] = acc;
-      }
-    T w3[2][4];  // [i1][p2]
-#pragma unroll
-    for (int i1 = 0; i1 < 2; ++i1)
-#pragma unroll
-      for (int p2 = 0; p2 < 4; ++p2) {
-        T acc = T(0);
-#pragma unroll
-        for (int p1 = 0; p1 <= 3 - p2; ++p1) acc = fma(wn2[p3idx(p1, p2)], tb.PF[p1][i1], acc);
-        w3[i1][p2] = acc;
-      }
-    // G part per face time point
-    T gv[2][2][2];  // [it][i1][i2]
-#pragma unroll
-    for (int tq = 0; tq < 2; ++tq) {
-      const T* gtv = gt + (v * 2 + tq) * 10;
-      T gn2[6];  // (p1, p2) with p1 + p2 <= 2, index p2idx(p1, p2)
-#pragma unroll
-      for (int p2 = 0; p2 <= 2; ++p2)
-#pragma unroll
-        for (int p1 = 0; p1 <= 2 - p2; ++p1) {
-          T acc = T(0);
-#pragma unroll
-          for (int an = 0; an <= 2 - p1 - p2; ++an) {
-            const int m = d == 0 ? tri2idx(an, p1, p2) : d == 1 ? tri2idx(p1, an, p2) : tri2idx(p1, p2, an);
-            acc = fma(gtv[m], tb.PE[an][side], acc);
-          }
-          gn2[p2idx(p1, p2)] = acc;
-        }
-#pragma unroll
-      for (int i1 = 0; i1 < 2; ++i1) {
-        T g3[3];
-#pragma unroll
-        for (int p2 = 0; p2 < 3; ++p2) {
-          T acc = T(0);
-#pragma unroll
-          for (int p1 = 0; p1 <= 2 - p2; ++p1) acc = fma(gn2[p2idx(p1, p2)], tb.PF[p1][i1], acc);
-          g3[p2] = acc;
-        }
-#pragma unroll
-        for (int i2 = 0; i2 < 2; ++i2) {
-          T acc = T(0);
-#pragma unroll
-          for (int p2 = 0; p2 < 3; ++p2) acc = fma(g3[p2], tb.PF[p2][i2], acc);
-          gv[tq][i1][i2] = acc;
-        }
-      }
-    }
-#pragma unroll
-    for (int i1 = 0; i1 < 2; ++i1)
-#pragma unroll
-      for (int i2 = 0; i2 < 2; ++i2) {
-        T acc = T(0);
-#pragma unroll
-        for (int p2 = 0; p2 < 4; ++p2) acc = fma(w3[i1][p2], tb.PF[p2][i2], acc);
-#pragma unroll
-        for (int tq = 0; tq < 2; ++tq) fv[(ds * 8 + i1 + 2 * (i2 + 2 * tq)) * 5 + v] = acc - gv[tq][i1][i2];
-      }
-  }
+  if (lane < 30) face_values_one<T>(sw, gt, fv, tb, lane % 5, lane / 5);
   __syncwarp();
   bool bad = false;
   if (q.fallback)
@@ -1259,7 +1273,9 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
 
   // the modes of the next zone pair are loaded while this one is computed
   // (a zone beyond the box reads a uniform state and stores nothing)
-  const long long rstep = (long long)gridDim.x * LW * 2;
+  constexpr int ZPB = 2 * LW;   // zones per block, consecutive
+  const long long rstep = (long long)gridDim.x * ZPB;
+  __shared__ unsigned char s_bad[ZPB];   // positivity fallback per zone of the block
   float wpre[7];
   auto fetch = [&](long long rr) {
 #pragma unroll
@@ -1268,9 +1284,12 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
       wpre[k] = it < 100 && rr < nb ? W[(long long)it * nb + rr] : (it == 0 || it == 80 ? 1.f : 0.f);
     }
   };
-  long long r0 = ((long long)blockIdx.x * LW + wib) * 2;
+  // the loop is uniform over the block (its zones are stored together at the
+  // end of an iteration); zones beyond the box compute on the uniform state
+  long long r0 = (long long)blockIdx.x * ZPB + 2 * wib;
   fetch(r0 + zh);
-  for (; r0 < nb; r0 += rstep) {
+  for (long long rb = (long long)blockIdx.x * ZPB; rb < nb; rb += rstep, r0 += rstep) {
+    const bool live = r0 + zh < nb;   // this lane's zone exists
 #pragma unroll
     for (int k = 0; k < 7; ++k)
       if (l16 + 16 * k < 100) sw[l16 + 16 * k] = wpre[k];
@@ -1404,15 +1423,40 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
       __syncwarp();
       line_project<2>(y2, y3, sg, sw, tb, ix, l16, lam);
     }
-    // face states, one zone after the other, with the whole warp
-#pragma unroll 1
-    for (int zz = 0; zz < 2; ++zz) {
-      const long long rz = r0 + zz;
-      if (rz >= nb) break;
-      fact_face_states<float, 16>(q, wbase + LineSmem::W + zz * LineSmem::WS, wbase + LineSmem::G + zz * LineSmem::GS,
-                                  wbase + LineSmem::Y2 + zz * LineSmem::Y2S, tb, lane, gm1, nb, rz, FS);
-      __syncwarp();
+    // Face values of the warp's two zones at once: lane l16 of a zone takes the
+    // (variable, direction-side) combinations l16 and l16 + 16 (< 30); the
+    // zone's z-projected flux rows are dead and hold the face values (240) and
+    // the time-integrated G (100)
+    face_gt<float, 16>(sg, y2 + 240, tb, l16, 16);
+    __syncwarp();
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int c = l16 + 16 * cc;
+      if (c < 30) face_values_one<float>(sw, y2 + 240, y2, tb, c % 5, c / 5);
     }
+    __syncwarp();
+    bool bad = false;
+    if (q.fallback)
+      for (int row = l16; row < 48; row += 16) bad = bad || !state_physical5<float>(y2 + row * 5, gm1);
+    const unsigned ballot = __ballot_sync(0xffffffffu, bad);
+    const bool zbad = q.fallback && live && ((ballot >> (16 * zh)) & 0xffffu) != 0;
+    if (l16 == 0) s_bad[2 * wib + zh] = zbad ? 1 : 0;
+    if (zbad && l16 == 0 && q.fb_count) atomicAdd(q.fb_count, 1ULL);
+    __syncthreads();
+    // the block's consecutive zones stored together: neighbouring threads write
+    // neighbouring zones of one (face row, variable), so a warp's store covers
+    // eight entries of four zones instead of 32 entries of one
+    for (int it = threadIdx.x; it < 240 * ZPB; it += blockDim.x) {
+      const int zb = it % ZPB, e = it / ZPB;
+      const long long rz = rb + zb;
+      if (rz < nb) {
+        const float* zw = smem + (zb >> 1) * LineSmem::SIZE;
+        const int zz = zb & 1;
+        FS[(long long)e * nb + rz] = s_bad[zb] ? zw[LineSmem::W + zz * LineSmem::WS + (e % 5) * 20]
+                                               : zw[LineSmem::Y2 + zz * LineSmem::Y2S + e];
+      }
+    }
+    __syncthreads();
   }
 }
 
