@@ -440,6 +440,29 @@ __device__ __forceinline__ void weno1d(const T* d, const double* lin, double eps
                                        T* out) {
   T c[N + 1][N];
   weno_candidates<N, T>(d, c);
+  if constexpr (sizeof(T) == 4) {
+    if (!linear) {
+      // FP32 form: the epsilon path, t_k = eps + beta_k and t_k^2, in FP64;
+      // the weights lin_k / t_k^2, normalised, in FP32 (t_k^2 >= eps^2 = 1e-24
+      // and lin_k / t_k^2 <= 1e24 lie well inside the FP32 range)
+      float q[N + 1], sum = 0.f;
+#pragma unroll
+      for (int k = 0; k <= N; ++k) {
+        const double t = eps + (double)weno_beta<N, T>(c[k]);
+        q[k] = (float)lin[k] / (float)(t * t);
+        sum += q[k];
+      }
+      const float inv = 1.f / sum;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        float acc = (q[0] * inv) * c[0][a];
+#pragma unroll
+        for (int k = 1; k <= N; ++k) acc = fmaf(q[k] * inv, c[k][a], acc);
+        out[a] = acc;
+      }
+      return;
+    }
+  }
   double om[N + 1];
   if (linear) {
 #pragma unroll
