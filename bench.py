@@ -553,7 +553,7 @@ def run_native(args, rank, world, local):
         np32, mp32 = prof32["predictor"]
         g32.close()
         f32 = {"value": world * zones * args.steps / (ms32 * 1e-3), "ms_per_step": ms32 / args.steps,
-               "dtype": "f32 bulk, f64 update/weights/CFL",
+               "dtype": "f32 bulk, f64 update/WENO epsilon path/CFL",
                "predictor_ms": mp32 / max(np32, 1),
                "predictor_tflops": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12,
                "predictor_frac_fp32_peak": flops_pred / (mp32 / max(np32, 1) * 1e-3) / 1e12 / PEAK_FP32}
