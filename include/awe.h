@@ -70,10 +70,10 @@ typedef enum {
 typedef enum {
   AWE_FP64 = 0,       /* every stage in FP64 */
   AWE_FP32_BULK = 1   /* reconstruction, predictor and Riemann fluxes in FP32;
-                         the WENO epsilon path (eps + beta_k and its square),
-                         the conserved-variable update and the CFL reduction
-                         in FP64; the weights formed from the epsilon path in
-                         FP32 */
+                         the WENO epsilon path (eps + beta_k), the differences
+                         of the zone means, the conserved-variable update and
+                         the CFL reduction in FP64; the weights formed from
+                         eps + beta_k in FP32 */
 } awe_prec;
 
 /* Riemann solvers of the corrector (Sec. I.1 names HLLC, HLL, HLLEM and

@@ -15,7 +15,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libawe.so")
 SOURCES = ["awe_api.cu", "awe_bc.cu", "awe_recon.cu", "awe_predict.cu", "awe_flux.cu",
            "awe_gate.cu", "awe_tables.cu", "awe_peaks.cu", "awe_noalloc.cu", "awe_rk.cu"]
-HEADERS = ["awe_internal.cuh", "awe_flux.cuh", "awe_rk.h", "awe_tables.h", "awe_gate.h", "predict_index.cuh", "stencils.inc"]
+HEADERS = ["awe_internal.cuh", "fp_bits.cuh", "awe_flux.cuh", "awe_rk.h", "awe_tables.h", "awe_gate.h", "predict_index.cuh", "stencils.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without FMA contraction, so that host-side tables round the same
 # way on x86-64 and AArch64

@@ -537,7 +537,10 @@ int awe_create(const awe_config* cfg, void* stream, awe_grid** out) {
   q.gamma = c.gamma;
   q.eps = c.weno_eps;
   q.cfl = c.cfl;
-  for (int k = 0; k < 4; ++k) q.lin[k] = c.lin[k];
+  for (int k = 0; k < 4; ++k) {
+    q.lin[k] = c.lin[k];
+    q.linf[k] = (float)c.lin[k];
+  }
   for (int f = 0; f < 6; ++f) {
     q.bc[f] = f < 2 * c.dim ? c.bc[f] : AWE_BC_PERIODIC;
     for (int v = 0; v < 5; ++v) q.inflow[f][v] = c.inflow[f][v];

@@ -33,20 +33,25 @@ __global__ void __launch_bounds__(256) k_update(Geo q, int z0, int z1, const dou
   bool bad = false;
   for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < nact;
        z += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(z % nx);
-    long long t = z / nx;
-    int j = (int)(t % ny);
-    int kk = (int)(t / ny);
+    int i, j, kk;
+    split3(z, (int)nx, (int)ny, i, j, kk);
     long long g = gidx(q, i, j, D == 3 ? kk + z0 : 0);
     long long f0 = ((long long)kk * ny + j) * (nx + 1) + i;
     long long f1 = ((long long)kk * (ny + 1) + j) * nx + i;
     long long f2 = ((long long)kk * ny + j) * nx + i;
+    // FP32 fluxes widen exactly by bit operations (f32_to_f64: the hardware
+    // conversion issues on the FP64 pipe; a subnormal flux counts as zero on
+    // both of its zones, so the update stays conservative)
+    auto wd = [](T x) -> double {
+      if constexpr (sizeof(T) == 8) return x;
+      else return f32_to_f64(x);
+    };
     double u[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double acc = lam[0] * ((double)F0[v * n0 + f0 + 1] - (double)F0[v * n0 + f0]);
-      acc += lam[1] * ((double)F1[v * n1 + f1 + nx] - (double)F1[v * n1 + f1]);
-      if (D == 3) acc += lam[2] * ((double)F2[v * n2 + f2 + nx * ny] - (double)F2[v * n2 + f2]);
+      double acc = lam[0] * (wd(F0[v * n0 + f0 + 1]) - wd(F0[v * n0 + f0]));
+      acc += lam[1] * (wd(F1[v * n1 + f1 + nx]) - wd(F1[v * n1 + f1]));
+      if (D == 3) acc += lam[2] * (wd(F2[v * n2 + f2 + nx * ny]) - wd(F2[v * n2 + f2]));
       u[v] = Uold[v * q.ntot + g] - acc;
       Unew[v * q.ntot + g] = u[v];
     }

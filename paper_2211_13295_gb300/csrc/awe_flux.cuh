@@ -40,10 +40,9 @@ __global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, 
   const T wq = T(1) / T(NFQ);  // tensor Gauss weights (1/2 per 2-point dimension, 1 for 1 point)
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
        f += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(f % E[0]);
-    long long t = f / E[0];
-    int j = (int)(t % E[1]);
-    int k = (int)(t / E[1]) + (D == 3 ? z0 : 0);
+    int i, j, k;
+    split3(f, E[0], E[1], i, j, k);
+    if (D == 3) k += z0;
     long long rz = box.index(i, j, k);
     long long lz = rz - (d == 0 ? 1 : d == 1 ? box.ext[0] : (long long)box.ext[0] * box.ext[1]);
     T acc[NV];

@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "../../include/awe.h"
+#include "fp_bits.cuh"
 
 namespace awe {
 
@@ -36,6 +37,7 @@ struct Geo {
   // lst[a][j] = sum_k lin[k] c_k[a][j] on the differences d[j] (j = 0..2N)
   double lst[3][7];
   float lstf[3][7];
+  float linf[4];   // lin in FP32 (the FP32 form's weights)
 };
 
 // index of an active-relative coordinate in a ghosted array
@@ -45,6 +47,25 @@ __host__ __device__ __forceinline__ long long gidx(const Geo& q, int i, int j, i
 }
 
 // A rectangular region of zones in active-relative coordinates, [lo, lo+ext).
+// r = (k e1 + j) e0 + i with 0 <= i < e0, 0 <= j < e1: unsigned 32-bit
+// divisions while r fits in 32 bits (a 64-bit division is a long software
+// sequence), 64-bit ones beyond
+__host__ __device__ __forceinline__ void split3(long long r, int e0, int e1, int& i, int& j, int& k) {
+  if (r >= 0 && r <= 0xffffffffLL) {
+    const unsigned u = (unsigned)r, t = u / (unsigned)e0;
+    i = (int)(u - t * (unsigned)e0);
+    const unsigned kq = t / (unsigned)e1;
+    j = (int)(t - kq * (unsigned)e1);
+    k = (int)kq;
+  } else {
+    const long long t = r / e0;
+    i = (int)(r - t * e0);
+    const long long kq = t / e1;
+    j = (int)(t - kq * e1);
+    k = (int)kq;
+  }
+}
+
 struct Region {
   int lo[3], ext[3];
   __host__ __device__ __forceinline__ long long size() const {
@@ -54,10 +75,10 @@ struct Region {
     return ((long long)(k - lo[2]) * ext[1] + (j - lo[1])) * ext[0] + (i - lo[0]);
   }
   __host__ __device__ __forceinline__ void coords(long long r, int& i, int& j, int& k) const {
-    i = lo[0] + (int)(r % ext[0]);
-    long long t = r / ext[0];
-    j = lo[1] + (int)(t % ext[1]);
-    k = lo[2] + (int)(t / ext[1]);
+    split3(r, ext[0], ext[1], i, j, k);
+    i += lo[0];
+    j += lo[1];
+    k += lo[2];
   }
 };
 
@@ -436,20 +457,22 @@ __device__ __forceinline__ void linear1d(const T* d, const T (*lst)[7], T* out) 
 }
 
 template <int N, typename T>
-__device__ __forceinline__ void weno1d(const T* d, const double* lin, double eps, bool linear,
-                                       T* out) {
+__device__ __forceinline__ void weno1d(const T* d, const double* lin, const float* linf, double eps,
+                                       bool linear, T* out) {
   T c[N + 1][N];
   weno_candidates<N, T>(d, c);
   if constexpr (sizeof(T) == 4) {
     if (!linear) {
-      // FP32 form: the epsilon path, t_k = eps + beta_k and t_k^2, in FP64;
-      // the weights lin_k / t_k^2, normalised, in FP32 (t_k^2 >= eps^2 = 1e-24
-      // and lin_k / t_k^2 <= 1e24 lie well inside the FP32 range)
+      // FP32 form: the epsilon path, t_k = eps + beta_k, in FP64 (beta_k
+      // widened exactly, t_k narrowed toward zero, both by bit operations:
+      // fp_bits.cuh); the weights lin_k / t_k^2, normalised, in FP32
+      // (t_k^2 >= eps^2 = 1e-24 and lin_k / t_k^2 <= 1e24 lie well inside
+      // the FP32 range)
       float q[N + 1], sum = 0.f;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
-        const double t = eps + (double)weno_beta<N, T>(c[k]);
-        q[k] = (float)lin[k] / (float)(t * t);
+        const float t = f64_to_f32_rz(eps + nonneg_f32_to_f64(weno_beta<N, T>(c[k])));
+        q[k] = linf[k] / (t * t);
         sum += q[k];
       }
       const float inv = 1.f / sum;

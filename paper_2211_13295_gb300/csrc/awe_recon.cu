@@ -13,7 +13,8 @@
 //   pass Z on the box [-1,nx] x [-1,ny] x [z0-1, z1]:      the c >= 1 modes,
 // and the last pass (Y in 2D, Z in 3D) assembles all modes of the box zones.
 // Differences from the zone's own value are taken in FP64 for the zone means
-// and in T for mode fields; WENO weights are FP64 (see weno1d).
+// (rounded toward zero to FP32 in the FP32 form, mean_diff) and in T for mode
+// fields; the WENO epsilon path is FP64 (see weno1d).
 #include "awe_internal.cuh"
 
 namespace awe {
@@ -56,13 +57,19 @@ __device__ __forceinline__ void recon1d(const T* d, const Geo& q, bool linear, i
     if constexpr (sizeof(T) == 8) linear1d<N, T>(d, q.lst, out);
     else linear1d<N, T>(d, q.lstf, out);
   } else {
-    weno1d<N, T>(d, q.lin, q.eps, false, out);
+    weno1d<N, T>(d, q.lin, q.linf, q.eps, false, out);
   }
 }
 template <int N> __host__ __device__ constexpr int xy_index(int a, int b) {
   int idx = 0;
   for (int aa = 1; aa < a; ++aa) idx += N - aa;
   return idx + (b - 1);
+}
+
+// difference of two zone means (FP64) in T
+template <typename T> __device__ __forceinline__ T mean_diff(double a, double b) {
+  if constexpr (sizeof(T) == 8) return a - b;
+  else return f64_to_f32_rz(a - b);
 }
 
 __device__ __forceinline__ bool use_linear(const unsigned char* flags, const Geo& q, int i, int j,
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(128) k_recon_x(Geo q, Region rx, const double*
       double u0 = u[0];
       T d[2 * N + 1];
 #pragma unroll
-      for (int s = -N; s <= N; ++s) d[s + N] = (T)(u[s] - u0);
+      for (int s = -N; s <= N; ++s) d[s + N] = mean_diff<T>(u[s], u0);
       T out[N];
       recon1d<N, T>(d, q, lin, v, out);
 #pragma unroll
@@ -125,7 +132,7 @@ __global__ void __launch_bounds__(128) k_recon_y(Geo q, Region rx, Region ry, Re
       double u0 = u[0];
       T d[2 * N + 1];
 #pragma unroll
-      for (int s = -N; s <= N; ++s) d[s + N] = (T)(u[s * ystride] - u0);
+      for (int s = -N; s <= N; ++s) d[s + N] = mean_diff<T>(u[s * ystride], u0);
       T out[N];
       recon1d<N, T>(d, q, lin, v, out);
       if (!last) {
@@ -160,7 +167,7 @@ __global__ void __launch_bounds__(128) k_recon_y(Geo q, Region rx, Region ry, Re
 
 // ---------------------------------------------------------------------------
 template <int N, typename T>
-__global__ void __launch_bounds__(128) k_recon_z(Geo q, Region rx, Region ry, Region box,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 0) k_recon_z(Geo q, Region rx, Region ry, Region box,
                                                  const double* __restrict__ U,
                                                  const unsigned char* __restrict__ flags,
                                                  const T* __restrict__ X, const T* __restrict__ Y,
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(128) k_recon_z(Geo q, Region rx, Region ry, Re
       double u0 = u[0];
       T d[2 * N + 1];
 #pragma unroll
-      for (int s = -N; s <= N; ++s) d[s + N] = (T)(u[s * zstride] - u0);
+      for (int s = -N; s <= N; ++s) d[s + N] = mean_diff<T>(u[s * zstride], u0);
       T out[N];
       recon1d<N, T>(d, q, lin, v, out);
       Wp(v, 0, 0, 0) = (T)u0;
