@@ -101,6 +101,23 @@ template <int D, int N> struct Modes {
 // ---------------------------------------------------------------------------
 // Euler equations, ideal gas
 // ---------------------------------------------------------------------------
+// Division and square root of the FP32 form's predictor and Riemann fluxes:
+// the fast forms (__fdividef: within 2 ulp for a divisor of magnitude in
+// [2^-126, 2^126]; x rsqrtf(x): within 3 ulp for x > 0, 0 at 0, NaN below)
+// instead of the IEEE refinement sequences.  FP64 keeps the IEEE operations.
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+  else return a / b;
+}
+template <typename T> __device__ __forceinline__ T fsqrt(T x) {
+  if constexpr (sizeof(T) == 4) {
+    const float inf = __int_as_float(0x7f800000);
+    return x > 0.f ? (x < inf ? x * rsqrtf(x) : x) : x == 0.f ? 0.f : __int_as_float(0x7fffffff);
+  } else {
+    return sqrt(x);
+  }
+}
+
 template <int D, typename T>
 __device__ __forceinline__ T pressure_of(const T* U, T gm1) {
   T irho = T(1) / U[0];
@@ -132,13 +149,13 @@ __device__ __forceinline__ void phys_fluxes_irho(const T* U, T irho, T gm1, T F[
 }
 template <int D, typename T>
 __device__ __forceinline__ void phys_fluxes(const T* U, T gm1, T F[D][D + 2]) {
-  phys_fluxes_irho<D, T>(U, T(1) / U[0], gm1, F);
+  phys_fluxes_irho<D, T>(U, fdiv(T(1), U[0]), gm1, F);
 }
 // 1/a and 1/b from one division: 1/a = b / (ab), 1/b = a / (ab) (densities of
 // a pair of nodes; ab stays far inside the range for physical densities)
 template <typename T>
 __device__ __forceinline__ void recip_pair(T a, T b, T& ia, T& ib) {
-  const T r = T(1) / (a * b);
+  const T r = fdiv(T(1), a * b);
   ia = b * r;
   ib = a * r;
 }
@@ -166,10 +183,10 @@ __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma,
   }
   T El = UL[D + 1], Er = UR[D + 1];
   T pl = gm1 * (El - T(0.5) * kl), pr = gm1 * (Er - T(0.5) * kr);
-  T cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+  T cl = fsqrt(gamma * pl * irl), cr = fsqrt(gamma * pr * irr);
   T ul = vl[dir], ur = vr[dir];
-  T sl = sqrt(rl), sr = sqrt(rr);
-  T iden = T(1) / (sl + sr);
+  T sl = fsqrt(rl), sr = fsqrt(rr);
+  T iden = fdiv(T(1), sl + sr);
   T vt2 = T(0), vtn = T(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -178,11 +195,11 @@ __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma,
     if (d == dir) vtn = vt;
   }
   T Ht = (sl * (El + pl) * irl + sr * (Er + pr) * irr) * iden;
-  T ct = sqrt(gm1 * (Ht - T(0.5) * vt2));
+  T ct = fsqrt(gm1 * (Ht - T(0.5) * vt2));
   T SL = fmin(ul - cl, vtn - ct);
   T SR = fmax(ur + cr, vtn + ct);
   T ml = rl * (SL - ul), mr = rr * (SR - ur);
-  T Ss = (pr - pl + ul * ml - ur * mr) / (ml - mr);
+  T Ss = fdiv(pr - pl + ul * ml - ur * mr, ml - mr);
   // branches in the order F_L (0 <= S_L), F*_L (0 <= S*), F*_R (0 < S_R), F_R
   if (T(0) <= SL) {
     F[0] = UL[1 + dir];
@@ -201,7 +218,7 @@ __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma,
     const T* U = left ? UL : UR;
     T S = left ? SL : SR, u = left ? ul : ur, m = left ? ml : mr, p = left ? pl : pr;
     T rho = left ? rl : rr, E = left ? El : Er, ir = left ? irl : irr;
-    T f = m / (S - Ss);
+    T f = fdiv(m, S - Ss);
     // F* = F(U) + S (U* - U)
     F[0] = U[1 + dir] + S * (f - rho);
 #pragma unroll
@@ -210,7 +227,7 @@ __device__ __forceinline__ void hllc(const T* UL, const T* UR, int dir, T gamma,
       F[1 + e] = U[1 + e] * u + S * (us - U[1 + e]);
     }
     F[1 + dir] += p;
-    T Es = f * (E * ir + (Ss - u) * (Ss + p / m));
+    T Es = f * (E * ir + (Ss - u) * (Ss + fdiv(p, m)));
     F[D + 1] = (E + p) * u + S * (Es - E);
   }
 }
@@ -256,10 +273,10 @@ __device__ __forceinline__ void hll_family(const T* UL, const T* UR, int dir, T 
   }
   T El = UL[D + 1], Er = UR[D + 1];
   T pl = gm1 * (El - T(0.5) * kl), pr = gm1 * (Er - T(0.5) * kr);
-  T cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+  T cl = fsqrt(gamma * pl * irl), cr = fsqrt(gamma * pr * irr);
   T ul = vl[dir], ur = vr[dir];
-  T sl = sqrt(rl), sr = sqrt(rr);
-  T iden = T(1) / (sl + sr);
+  T sl = fsqrt(rl), sr = fsqrt(rr);
+  T iden = fdiv(T(1), sl + sr);
   T vt[D], vt2 = T(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -267,7 +284,7 @@ __device__ __forceinline__ void hll_family(const T* UL, const T* UR, int dir, T 
     vt2 = fma(vt[d], vt[d], vt2);
   }
   T Ht = (sl * (El + pl) * irl + sr * (Er + pr) * irr) * iden;
-  T ct = sqrt(gm1 * (Ht - T(0.5) * vt2));
+  T ct = fsqrt(gm1 * (Ht - T(0.5) * vt2));
   T SL = fmin(ul - cl, vt[dir] - ct);
   T SR = fmax(ur + cr, vt[dir] + ct);
   if (T(0) <= SL) {
@@ -285,8 +302,8 @@ __device__ __forceinline__ void hll_family(const T* UL, const T* UR, int dir, T 
   for (int s = 0; s < NV; ++s) jump[s] = UR[s] - UL[s];
   if (EM) {
     const T ut = vt[dir];
-    const T delta = T(1) - fmin(ut, T(0)) / SL - fmax(ut, T(0)) / SR;
-    const T ac = delta * ((rr - rl) - (pr - pl) / (ct * ct));
+    const T delta = T(1) - fdiv(fmin(ut, T(0)), SL) - fdiv(fmax(ut, T(0)), SR);
+    const T ac = delta * ((rr - rl) - fdiv(pr - pl, ct * ct));
     jump[0] -= ac;
 #pragma unroll
     for (int e = 0; e < D; ++e) jump[1 + e] -= ac * vt[e];
@@ -300,7 +317,7 @@ __device__ __forceinline__ void hll_family(const T* UL, const T* UR, int dir, T 
       jump[D + 1] -= at * vt[t];
     }
   }
-  const T inv = T(1) / (SR - SL), slsr = SL * SR;
+  const T inv = fdiv(T(1), SR - SL), slsr = SL * SR;
 #pragma unroll
   for (int s = 0; s < NV; ++s) F[s] = (SR * FL[s] - SL * FR[s] + slsr * jump[s]) * inv;
 }
@@ -326,7 +343,7 @@ __device__ __forceinline__ void rusanov(const T* UL, const T* UR, int dir, T gam
     kr = fma(UR[1 + d], vr[d], kr);
   }
   T pl = gm1 * (UL[D + 1] - T(0.5) * kl), pr = gm1 * (UR[D + 1] - T(0.5) * kr);
-  T S = fmax(fabs(vl[dir]) + sqrt(gamma * pl * irl), fabs(vr[dir]) + sqrt(gamma * pr * irr));
+  T S = fmax(fabs(vl[dir]) + fsqrt(gamma * pl * irl), fabs(vr[dir]) + fsqrt(gamma * pr * irr));
   T FL[NV], FR[NV];
   dir_flux<D, T>(UL, vl, pl, dir, FL);
   dir_flux<D, T>(UR, vr, pr, dir, FR);
@@ -465,17 +482,19 @@ __device__ __forceinline__ void weno1d(const T* d, const double* lin, const floa
     if (!linear) {
       // FP32 form: the epsilon path, t_k = eps + beta_k, in FP64 (beta_k
       // widened exactly, t_k narrowed toward zero, both by bit operations:
-      // fp_bits.cuh); the weights lin_k / t_k^2, normalised, in FP32
-      // (t_k^2 >= eps^2 = 1e-24 and lin_k / t_k^2 <= 1e24 lie well inside
-      // the FP32 range)
+      // fp_bits.cuh); the weights lin_k / t_k^2, normalised, in FP32 with
+      // the fast reciprocal (t_k >= eps = 1e-12, so lin_k / t_k^2 <= 1e24;
+      // for t_k above ~1e19 the term underflows, as the IEEE form's t_k^2
+      // overflows)
       float q[N + 1], sum = 0.f;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
         const float t = f64_to_f32_rz(eps + nonneg_f32_to_f64(weno_beta<N, T>(c[k])));
-        q[k] = linf[k] / (t * t);
+        const float u = __fdividef(1.f, t);
+        q[k] = linf[k] * (u * u);
         sum += q[k];
       }
-      const float inv = 1.f / sum;
+      const float inv = __fdividef(1.f, sum);
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         float acc = (q[0] * inv) * c[0][a];

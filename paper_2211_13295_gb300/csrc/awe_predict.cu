@@ -1336,7 +1336,7 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
         float qn[5], f1[9], f[9][3];
 #pragma unroll
         for (int v = 0; v < 5; ++v) qn[v] = wn[v][k];
-        sym_fluxes<float>(qn, 1.f / qn[0], gm1, f1);
+        sym_fluxes<float>(qn, __fdividef(1.f, qn[0]), gm1, f1);   // as recip_pair
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr) f[rr][0] = f[rr][1] = f[rr][2] = f1[rr];
         line_z_accumulate<0>(Z, f, k);
