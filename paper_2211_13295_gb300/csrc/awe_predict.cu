@@ -611,7 +611,8 @@ __device__ __forceinline__ void face_gt(const T* sg, T* gt, const Tabs<T>& tb, i
 // w part and, per face time point, the G part.  fv[(ds*8 + q)*5 + v], q = i1 +
 // 2*(i2 + 2*it), as the probes document.
 template <typename T>
-__device__ __forceinline__ void face_values_one(const T* sw, const T* gt, T* fv, const Tabs<T>& tb, int v, int ds) {
+__device__ __forceinline__ void face_values_reg(const T* sw, const T* gt, const Tabs<T>& tb, int v, int ds,
+                                                T (&out)[8]) {
   const int d = ds >> 1, side = ds & 1;
   // axes: n = d (normal), t1 < t2 the transverse ones.  Every loop below
   // is unrolled over compile-time exponents; the mode index of (an on the
@@ -686,8 +687,42 @@ __device__ __forceinline__ void face_values_one(const T* sw, const T* gt, T* fv,
 #pragma unroll
       for (int p2 = 0; p2 < 4; ++p2) acc = fma(w3[i1][p2], tb.PF[p2][i2], acc);
 #pragma unroll
-      for (int tq = 0; tq < 2; ++tq) fv[(ds * 8 + i1 + 2 * (i2 + 2 * tq)) * 5 + v] = acc - gv[tq][i1][i2];
+      for (int tq = 0; tq < 2; ++tq) out[i1 + 2 * (i2 + 2 * tq)] = acc - gv[tq][i1][i2];
     }
+}
+// stores fv[(ds*8 + q)*5 + v], q = i1 + 2*(i2 + 2*it), as the probes document
+template <typename T>
+__device__ __forceinline__ void face_values_store(T* fv, int v, int ds, const T (&out)[8]) {
+#pragma unroll
+  for (int qq = 0; qq < 8; ++qq) fv[(ds * 8 + qq) * 5 + v] = out[qq];
+}
+template <typename T>
+__device__ __forceinline__ void face_values_one(const T* sw, const T* gt, T* fv, const Tabs<T>& tb, int v, int ds) {
+  T out[8];
+  face_values_reg<T>(sw, gt, tb, v, ds, out);
+  face_values_store<T>(fv, v, ds, out);
+}
+
+// face_gt for one zone on 16 lanes: lanes l < 10 own (v, it) = (l >> 1, l & 1)
+// and every triple with compile-time indices
+template <typename T, int GS>
+__device__ __forceinline__ void face_gt_vt(const T* sg, T* gt, const Tabs<T>& tb, int l) {
+  if (l < 10) {
+    const int v = l >> 1, tq = l & 1;
+    T itf[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) itf[e] = tb.ITF[e][tq];
+    const T* g = sg + v * GS;
+    T* o = gt + (v * 2 + tq) * 10;
+#pragma unroll
+    for (int tr = 0; tr < 10; ++tr) {
+      const int a = tri2_p(tr), b = tri2_q(tr), c = tri2_r(tr);
+      T acc = T(0);
+#pragma unroll
+      for (int e = 0; e <= 2 - a - b - c; ++e) acc = fma(g[gmidx(a, b, c, e)], itf[e], acc);
+      o[tr] = acc;
+    }
+  }
 }
 
 template <typename T, int GS>
@@ -1427,12 +1462,18 @@ __global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, co
     // (variable, direction-side) combinations l16 and l16 + 16 (< 30); the
     // zone's z-projected flux rows are dead and hold the face values (240) and
     // the time-integrated G (100)
-    face_gt<float, 16>(sg, y2 + 240, tb, l16, 16);
+    face_gt_vt<float, 16>(sg, y2 + 240, tb, l16);
     __syncwarp();
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int c = l16 + 16 * cc;
-      if (c < 30) face_values_one<float>(sw, y2 + 240, y2, tb, c % 5, c / 5);
+    {
+      // both combinations evaluated before either is stored, so that their
+      // independent chains interleave (lanes 14, 15 repeat combination 29
+      // and store only their first)
+      const int c0 = l16, c1 = l16 + 16 < 30 ? l16 + 16 : 29;
+      float o0[8], o1[8];
+      face_values_reg<float>(sw, y2 + 240, tb, c0 % 5, c0 / 5, o0);
+      face_values_reg<float>(sw, y2 + 240, tb, c1 % 5, c1 / 5, o1);
+      face_values_store<float>(y2, c0 % 5, c0 / 5, o0);
+      if (l16 + 16 < 30) face_values_store<float>(y2, c1 % 5, c1 / 5, o1);
     }
     __syncwarp();
     bool bad = false;
