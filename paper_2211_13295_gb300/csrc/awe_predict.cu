@@ -1159,11 +1159,23 @@ struct LineSmem {
   static constexpr int SIZE = Y3 + 2 * Y3S - 4;              // 4220 per warp
 };
 
-// mass-row sources of the line kernel: as FactIdx::mass_src, with the g rows
-// 16 floats apart
+// Lane tables of the line kernel (copied to shared memory once per block).
+// The mass row of G-mode b, direction d: the sources of FactIdx::mass_src
+// with the g rows 16 floats apart, every offset valid (a g source that does
+// not exist reads entry 15 of g row 0, which stays 0; a w source that does
+// not exist reads w[0] and meets a zero factor: ms_fac where the momentum
+// mode one degree up is missing, ms_c3 where the mode three degrees up is),
+// and the coefficients (cw, c0, c1, c2) of the G-mode's time index; the last
+// projection step's factor c + 1 of G-mode b.  No branch and no conversion
+// in the kernel.
 struct LineIdx {
-  uint8_t mass_src[3][6][16];
+  uint8_t ms_off[3][5][16];   // w, g0, g1, g2 (from zg), w3 (from zw)
+  float ms_fac[3][16];        // 1, 2 or 3 (0: no source)
+  float ms_c3[3][16];         // 0.1 or 0
+  float ms_coef[16][4];       // cw, c0, c1, c2
+  float lp_cfac[16];          // c + 1
 };
+static_assert(offsetof(LineIdx, ms_coef) % 16 == 0, "float4 rows");
 __constant__ LineIdx c_lidx;
 // I_e(tau_t) P_c(z_k) for (c, e) = (1, 0), (1, 1), (2, 0): [j][t][k]
 __constant__ float c_ln_itpn[3][4][4];
@@ -1171,22 +1183,17 @@ __constant__ float c_ln_itpn[3][4][4];
 // mass row of G-mode b, direction d (line kernel layout): as mass_gmode_dir
 __device__ __forceinline__ float line_mass_dir(const float* zw, const float* zg, const LineIdx& ix, int b, int d,
                                                float lamd) {
-  const int e = unpack(kGmE, 2, b);
-  const int ow = ix.mass_src[d][0][b], o0 = ix.mass_src[d][1][b], o1 = ix.mass_src[d][2][b];
-  const int o2 = ix.mass_src[d][3][b], o3 = ix.mass_src[d][4][b];
-  const float w = ow != 255 ? zw[ow] : 0.f;
-  const float g0 = o0 != 255 ? zg[o0] : 0.f;
-  const float g1 = o1 != 255 ? zg[o1] : 0.f;
-  const float g2 = o2 != 255 ? zg[o2] : 0.f;
-  const float w3 = o3 != 255 ? zw[o3] : 0.f;
-  const float cw = e == 0 ? 1.f : 0.f;
-  const float c0 = e == 2 ? 0.f : -0.5f;
-  const float c1 = e == 0 ? 1.f / 6.f : e == 2 ? -1.f / 6.f : 0.f;
-  const float c2 = e == 1 ? 0.1f : 0.f;
-  const float m = fmaf(c2, g2, fmaf(c1, g1, fmaf(c0, g0, cw * w)));
-  return lamd * fmaf((float)ix.mass_src[d][5][b], m, 0.1f * w3);
+  const float w = zw[ix.ms_off[d][0][b]];
+  const float g0 = zg[ix.ms_off[d][1][b]], g1 = zg[ix.ms_off[d][2][b]], g2 = zg[ix.ms_off[d][3][b]];
+  const float w3 = zw[ix.ms_off[d][4][b]];
+  const float4 cf = *reinterpret_cast<const float4*>(ix.ms_coef[b]);
+  const float m = fmaf(cf.w, g2, fmaf(cf.z, g1, fmaf(cf.y, g0, cf.x * w)));
+  return lamd * fmaf(ix.ms_fac[d][b], m, ix.ms_c3[d][b] * w3);
 }
 
+__device__ __forceinline__ float dot4v(float4 a, float4 b) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
 __device__ __forceinline__ float dot4(float4 a, const float* bp) {
   const float4 b = *reinterpret_cast<const float4*>(bp);
   return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
@@ -1214,8 +1221,14 @@ __device__ __forceinline__ void line_project(const float* y2, float* y3, float* 
       const int s = ln_round_slot(R, u);
       if (ln_e(s) > EMAX) continue;
       float y[4];
+      if (R == 1) {
+        // contiguous: one 16-byte load (row bases and slots are multiples of 4 floats)
+        const float4 t4 = *reinterpret_cast<const float4*>(y2 + rb + s * 16 + 4 * m);
+        y[0] = t4.x; y[1] = t4.y; y[2] = t4.z; y[3] = t4.w;
+      } else {
 #pragma unroll
-      for (int n = 0; n < 4; ++n) y[n] = y2[rb + s * 16 + (R == 1 ? n + 4 * m : m + 4 * n)];
+        for (int n = 0; n < 4; ++n) y[n] = y2[rb + s * 16 + m + 4 * n];
+      }
 #pragma unroll
       for (int qq = 0; qq <= ln_qmax(R, s); ++qq) {
         float acc = y[0] * tc.WPN[qq][0];
@@ -1226,25 +1239,31 @@ __device__ __forceinline__ void line_project(const float* y2, float* y3, float* 
     }
   }
   __syncwarp();
-  // last step: G-modes b = m, m + 4, m + 8, m + 12 of variable 1 + vv
+  // last step: lane l16 takes G-mode b = l16 of the four variables 1..4,
+  // so that the mode's indices and its three basis rows are fetched once
+  if (l16 < NGE) {
+    const int b = l16;
+    const int a = unpack(kGmA, 2, b), bb = unpack(kGmB, 2, b);
+    const int slack = unpack(kLnSlack, 4, b);
+    const float4 q0 = *reinterpret_cast<const float4*>(tb.QN[a][slack]);
+    const float4 q1 = *reinterpret_cast<const float4*>(tb.QN[bb][slack]);
+    const float4 pz = *reinterpret_cast<const float4*>(tb.WPN[a]);
+    const float cf = ix.lp_cfac[b];
+    // y3[((R * 4 + vv) * 10 + tri) * 4 + m]: variable stride 40 floats
+    const float* y0 = y3 + unpack(kLnT0, 4, b) * 4;
+    const float* y1 = y3 + (40 + unpack(kLnT1, 4, b)) * 4;
+    const float* yz = y3 + (80 + unpack(kLnT2, 4, b)) * 4;
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    const int b = m + 4 * kk;
-    if (b < NGE) {
-      const int a = unpack(kGmA, 2, b), bb = unpack(kGmB, 2, b), c = unpack(kGmC, 2, b);
-      const int slack = unpack(kLnSlack, 4, b);
-      const float4 Y0 = *reinterpret_cast<const float4*>(y3 + ((0 * 4 + vv) * 10 + unpack(kLnT0, 4, b)) * 4);
-      const float4 Y1 = *reinterpret_cast<const float4*>(y3 + ((1 * 4 + vv) * 10 + unpack(kLnT1, 4, b)) * 4);
-      const float4 Yz = *reinterpret_cast<const float4*>(y3 + ((2 * 4 + vv) * 10 + unpack(kLnT2, 4, b)) * 4);
-      const float s0 = dot4(Y0, tb.QN[a][slack]);
-      const float s1 = dot4(Y1, tb.QN[bb][slack]);
-      float s2 = (float)(c + 1) * dot4(Yz, tb.WPN[a]);
+    for (int v4 = 0; v4 < 4; ++v4) {
+      const float s0 = dot4v(*reinterpret_cast<const float4*>(y0 + 40 * v4), q0);
+      const float s1 = dot4v(*reinterpret_cast<const float4*>(y1 + 40 * v4), q1);
+      float s2 = cf * dot4v(*reinterpret_cast<const float4*>(yz + 40 * v4), pz);
       if (b == 0) {
         // dP3 = 3 P2 + P0/10: the z-mode 3 coefficient also feeds c = 0
-        const float4 Y3z = *reinterpret_cast<const float4*>(y3 + ((2 * 4 + vv) * 10 + ln_tri(2, 3, 0)) * 4);
+        const float4 Y3z = *reinterpret_cast<const float4*>(y3 + (80 + ln_tri(2, 3, 0)) * 4 + 40 * v4);
         s2 = fmaf(0.1f, dot4(Y3z, tb.WPN[0]), s2);
       }
-      sg[(vv + 1) * 16 + b] = fmaf(lam[0], s0, fmaf(lam[1], s1, lam[2] * s2));
+      sg[(v4 + 1) * 16 + b] = fmaf(lam[0], s0, fmaf(lam[1], s1, lam[2] * s2));
     }
   }
   if (l16 < NGE) sg[l16] = gmass;
@@ -1536,13 +1555,27 @@ static cudaError_t upload_fact_indices(cudaStream_t s) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_fidx, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
   // the same sources for the line kernel, whose g rows are 16 floats apart
   LineIdx hl;
+  memset(&hl, 0, sizeof(hl));
   for (int d = 0; d < 3; ++d)
-    for (int k = 0; k < 6; ++k)
-      for (int b = 0; b < 16; ++b) {
-        uint8_t o = h.mass_src[d][k][b];
-        if (k >= 1 && k <= 3 && o != 255) o = (uint8_t)((o / 15) * 16 + o % 15);
-        hl.mass_src[d][k][b] = o;
+    for (int b = 0; b < 16; ++b) {
+      const uint8_t ow = h.mass_src[d][0][b], o3 = h.mass_src[d][4][b];
+      hl.ms_off[d][0][b] = ow != 255 ? ow : 0;
+      for (int k = 1; k <= 3; ++k) {
+        const uint8_t o = h.mass_src[d][k][b];
+        hl.ms_off[d][k][b] = o != 255 ? (uint8_t)((o / 15) * 16 + o % 15) : 15;
       }
+      hl.ms_off[d][4][b] = o3 != 255 ? o3 : 0;
+      hl.ms_fac[d][b] = (float)h.mass_src[d][5][b];   // 0 where ow is missing
+      hl.ms_c3[d][b] = o3 != 255 ? 0.1f : 0.f;
+    }
+  for (int b = 0; b < 15; ++b) {
+    const int ee = g[b][3];
+    hl.ms_coef[b][0] = ee == 0 ? 1.f : 0.f;
+    hl.ms_coef[b][1] = ee == 2 ? 0.f : -0.5f;
+    hl.ms_coef[b][2] = ee == 0 ? 1.f / 6.f : ee == 2 ? -1.f / 6.f : 0.f;
+    hl.ms_coef[b][3] = ee == 1 ? 0.1f : 0.f;
+    hl.lp_cfac[b] = (float)(g[b][2] + 1);
+  }
   if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_lidx, &hl, sizeof(hl), 0, cudaMemcpyHostToDevice, s);
   {
     Tabs<double> td[3];
