@@ -28,8 +28,13 @@ __host__ __device__ __forceinline__ int rotated_var(int r, int d) {
   return d == 2 ? 2 : 3;  // r == 3 (3D)
 }
 
+// Occupancy: the FP32 kernel waits on its loads of the face states (one
+// launch reads ~0.3 GB at 256^3), so it takes as many resident warps as its
+// registers allow without spilling (HLLC at 8 points: 64 registers, 32 warps
+// per SM; 8.0 -> 4.6 ms per 256^3 step against the compiler's 168
+// registers); FP64 is bound by its FP64 arithmetic and keeps the default.
 template <int D, int N, typename T, int K, int NP>
-__global__ void __launch_bounds__(128) k_flux(Geo q, Region box, int d, int z0, int z1,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (K == 0 ? (NP == 8 ? 8 : 6) : K == 2 ? 4 : K == 3 ? (D == 3 ? 5 : 6) : 6) : 0) k_flux(Geo q, Region box, int d, int z0, int z1,
                                               const T* __restrict__ FS, T* __restrict__ F) {
   constexpr int NV = D + 2, NFQ = NP;
   int E[3];
