@@ -1285,7 +1285,7 @@ __device__ __forceinline__ void line_z_accumulate(float (&Z)[9][9], const float 
 }
 
 template <int LW>
-__global__ void __launch_bounds__(32 * LW) k_predict_lines(Geo q, Region box, const float* __restrict__ W,
+__global__ void __launch_bounds__(32 * LW, 6) k_predict_lines(Geo q, Region box, const float* __restrict__ W,
                                                            const double* __restrict__ d_dt, int picard,
                                                            float* __restrict__ FS) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
